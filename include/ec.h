@@ -1,0 +1,195 @@
+/*
+ * ec.h -- C ABI of libec: Euler-characteristic, perimeter, area and volume
+ * curves of 2D / 3D fields on one NVIDIA GB300 (sm_103a), by vertex
+ * contributions (Laky & Zavala, arXiv 2311.11740).
+ *
+ * Problem statement (Sec. 2): a field of w x h pixels (2D) or w x h x d voxels
+ * (3D) is the top-cell layer of a closed cubical complex.  At filtration level
+ * t_k the complex holds every top cell with value <= t_k (Eq. sublevel_set)
+ * together with all of its faces, edges and vertices.  The EC curve is
+ * chi_k = V - E + F - C of that complex (Eq. EC_formula) for every level k.
+ * Perimeter, area and volume are the per-vertex descriptors of Tables 1 and 2.
+ * The library computes them from per-vertex contributions accumulated into a
+ * histogram over levels and prefix-summed (Sec. 2, Algorithms 1-3), exactly,
+ * in integers.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every function returns an int status (EC_OK = 0 or an EC_ERR_* code) and
+ *    never throws.  ec_last_error() returns a message for the calling thread's
+ *    most recent failure.
+ *  - Fields are C-contiguous, last dimension fastest: dims = {h, w} (2D) or
+ *    {d, h, w} (3D); element [y][x] / [z][y][x].  dims[i] >= 1.
+ *  - dtype: EC_U8, EC_U16 or EC_F32.  Thresholds are L values of the field's
+ *    type, non-decreasing.  NULL thresholds mean identity levels t_k = k
+ *    (integer dtypes only).  A top cell is active at level k iff
+ *    value <= t_k compared in the field's type (float32 for EC_F32; a NaN is
+ *    never active; -0.0 == +0.0).  1 <= L <= 65535; L == 0 is a no-op.
+ *  - descriptors: OR of EC_DESC_*; the output holds popcount(descriptors)
+ *    rows of L int64 values, rows ordered EC, PERIMETER, AREA, VOLUME.
+ *    Units: EC is the integer Euler characteristic; 2D perimeter counts unit
+ *    edges on the boundary of the active set; 2D area counts active pixels;
+ *    3D area counts unit faces on the boundary; 3D perimeter is the crease
+ *    length (Table 2's "Perimeter" column summed over vertices); volume counts
+ *    active voxels.  Cells outside the field are never active.
+ *  - connectivity: 2D 8 (the paper's choice, Sec. 2) or 4 (Table 1's 4-C
+ *    columns); 3D 26 (the paper's choice).  3D 6 -> EC_ERR_UNSUPPORTED.
+ *  - Device pointers (suffix _dev) must be device-accessible on the context's
+ *    device.  The caller owns every buffer; the library never frees caller
+ *    memory.  Work is ordered on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream) and results are valid once the stream has reached the
+ *    call's end.  One context's scratch memory serves one call in flight at a
+ *    time: give concurrent streams their own contexts.
+ */
+#ifndef EC_H
+#define EC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum ec_status {
+    EC_OK = 0,
+    EC_ERR_ARG = 1,          /* bad dims, L, pointer, descriptor/connectivity combination, unsorted thresholds */
+    EC_ERR_DTYPE = 2,        /* unknown dtype, or NULL thresholds with EC_F32 */
+    EC_ERR_UNSUPPORTED = 3,  /* valid request the library does not implement (3D 6-connectivity) */
+    EC_ERR_OOM = 4,          /* scratch allocation failed, or a memory cap / budget is too small */
+    EC_ERR_CUDA = 5,         /* a CUDA runtime call failed; ec_last_error() has its message */
+    EC_ERR_TIMEOUT = 6,      /* a bounded device or host wait gave up */
+    EC_ERR_OVERFLOW = 7,     /* an internal counter bound was exceeded (debug check) */
+    EC_ERR_BUSY = 8          /* server: no slot or memory free and the queue is full */
+};
+
+typedef enum { EC_U8 = 0, EC_U16 = 1, EC_F32 = 2 } ec_dtype;
+
+enum {
+    EC_DESC_EC = 1,
+    EC_DESC_PERIMETER = 2,
+    EC_DESC_AREA = 4,
+    EC_DESC_VOLUME = 8       /* 3D only */
+};
+
+typedef struct ec_ctx ec_ctx;
+
+/* Message of the calling thread's last failed call ("" if none).  The pointer
+ * stays valid until the thread's next ec_* call. */
+const char *ec_last_error(void);
+
+/* Create a context on CUDA device `device`: per-device tables, the plan
+ * cache and (grown on demand) scratch memory.  *ctx receives the handle. */
+int ec_ctx_create(ec_ctx **ctx, int device);
+/* Release everything the context owns.  Waits for its device to be idle. */
+int ec_ctx_destroy(ec_ctx *ctx);
+
+/* Tuning / checking options (ec_ctx_set_option).
+ *  EC_OPT_ALGO: 0 = auto (the fast per-voxel path), 1 = per-voxel regrouped
+ *    contributions (one histogram update per top cell), 2 = per-vertex
+ *    sorted contributions (Algorithms 1 and 3: sort the 4 or 8 values, add the
+ *    type change at each sorted value).  All give identical curves.
+ *  EC_OPT_VALIDATE: 1 = check device thresholds are non-decreasing (one
+ *    stream synchronisation per call; EC_ERR_ARG if not), 0 = trust them.
+ *  EC_OPT_TILE_Z: z planes per work item of the 3D kernels (0 = planner).
+ *  EC_OPT_GRID: blocks per launch (0 = planner).                           */
+enum { EC_OPT_ALGO = 1, EC_OPT_VALIDATE = 2, EC_OPT_TILE_Z = 3, EC_OPT_GRID = 4 };
+int ec_ctx_set_option(ec_ctx *ctx, int option, int64_t value);
+
+/* EC / perimeter / area curves of a 2D field resident on the device.
+ * field_dev: h*w values of `dtype`; thresholds_dev: L values of `dtype` or
+ * NULL (identity, integer dtypes); out_dev: int64 [popcount(descriptors)][L].
+ * Algorithms 1-2 of the paper, Table 1 weights. */
+int ec_curve_2d(ec_ctx *ctx, const void *field_dev, const int64_t dims[2], int dtype,
+                const void *thresholds_dev, int32_t L, int connectivity,
+                uint32_t descriptors, int64_t *out_dev, void *stream);
+
+/* EC / perimeter / area / volume curves of a 3D field resident on the device.
+ * Same conventions; dims = {d, h, w}.  Algorithm 3 of the paper (Appendix),
+ * Table 2 weights, 26-connectivity. */
+int ec_curve_3d(ec_ctx *ctx, const void *field_dev, const int64_t dims[3], int dtype,
+                const void *thresholds_dev, int32_t L, int connectivity,
+                uint32_t descriptors, int64_t *out_dev, void *stream);
+
+/* Low-memory 3D processing (Sec. 2.3 "Low-Memory Processing"): the field is
+ * never resident as a whole.  It is processed in z-slabs of `slab_planes`
+ * planes plus one halo plane on each side, with at most `device_mem_cap`
+ * bytes of device memory in use by this call (slab buffers, scratch and
+ * tables; 0 = no cap).  Slabs come either from `host_field` (a host pointer
+ * to the whole d*h*w field; page-locked memory overlaps copies with compute)
+ * or, when host_field is NULL, from `producer`, which must enqueue on
+ * `stream` the writing of planes [z0, z1) (z0 may be -1 and z1 may be d+1 to
+ * ask for halo planes outside the field: fill them with anything, they are
+ * ignored) into dst_dev (C-contiguous (z1-z0) x h x w of dtype) and return 0.
+ * thresholds_host: L values on the host (or NULL = identity).  out_host:
+ * int64 [popcount(descriptors)][L] on the host, written before return (the
+ * call is synchronous).  Results are bit-identical to ec_curve_3d. */
+typedef int (*ec_slab_fn)(void *user, int64_t z0, int64_t z1, void *dst_dev, void *stream);
+int ec_curve_3d_stream(ec_ctx *ctx, const void *host_field, ec_slab_fn producer, void *user,
+                       const int64_t dims[3], int dtype, const void *thresholds_host,
+                       int32_t L, int connectivity, uint32_t descriptors,
+                       int64_t slab_planes, size_t device_mem_cap, int64_t *out_host);
+
+/* One field of a batch or a served request. */
+typedef struct {
+    const void *field;        /* device pointer (ec_batch) or host/device pointer (server) */
+    int32_t ndim;             /* 2 or 3 */
+    int64_t dims[3];          /* {h, w, 0} or {d, h, w} */
+    int32_t dtype;            /* ec_dtype */
+    const void *thresholds;   /* device (ec_batch) / host (server) pointer, or NULL = identity */
+    int32_t L;
+    int32_t connectivity;
+    uint32_t descriptors;
+    int64_t *out;             /* device (ec_batch) / host (server): [popcount][L] int64 */
+} ec_field_desc;
+
+/* Curves of n independent fields of uneven sizes, dtypes and level counts in
+ * one persistent-kernel launch (Sec. 4 notes that small images parallelise
+ * poorly one at a time).  All pointers in `fields` are device pointers.
+ * Results are identical to n separate ec_curve_2d / ec_curve_3d calls. */
+int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, void *stream);
+
+/* Bytes of scratch memory ec_curve_2d / ec_curve_3d need for a request. */
+size_t ec_workspace_bytes(int dtype, int32_t ndim, const int64_t *dims, int32_t L,
+                          uint32_t descriptors);
+
+/* ------------------------------------------------------------------ serving
+ * A request loop that admits fields while earlier ones are on the GPU
+ * (continuous batching): a request is admitted when a slot is free and its
+ * device bytes fit in `device_mem_budget`; admitted requests are copied and
+ * computed on their own streams, so their work overlaps on the device.
+ * Request fields, thresholds and outputs are host pointers that must stay
+ * valid until the request is done.                                         */
+typedef struct ec_server ec_server;
+int ec_server_create(ec_ctx *ctx, size_t device_mem_budget, int32_t max_slots, ec_server **server);
+/* Queue a request; *ticket identifies it.  EC_ERR_BUSY if the pending queue
+ * is full; EC_ERR_OOM if the request alone exceeds the budget. */
+int ec_server_submit(ec_server *server, const ec_field_desc *request, uint64_t *ticket);
+/* *done = 1 once the request finished; *status is its ec_status. */
+int ec_server_poll(ec_server *server, uint64_t ticket, int *done, int32_t *status);
+/* Block until the request is done or timeout_ms passes (EC_ERR_TIMEOUT). */
+int ec_server_wait(ec_server *server, uint64_t ticket, int64_t timeout_ms, int32_t *status);
+/* Latency (submit to completion) and timing statistics of finished requests:
+ * out[0] = count, out[1] = p50 us, out[2] = p99 us, out[3] = mean us,
+ * out[4] = first-submit-to-last-completion us. */
+int ec_server_stats(ec_server *server, double out[5]);
+int ec_server_destroy(ec_server *server);
+
+/* ---------------------------------------------------- host-side inspection
+ * The per-vertex contribution tables the kernels use, derived at build time
+ * from the closed-complex rule (Tables 1 and 2 of the paper are what they
+ * must reproduce).  2D: out[16][4] = {4*EC(8-C), 4*EC(4-C), 2*perimeter,
+ * 4*area} per 4-bit neighbourhood mask (bit x + 2y).  3D: out[256][4] =
+ * {8*EC, 2*perimeter, 4*area, 8*volume} per 8-bit mask (bit x + 2y + 4z). */
+int ec_vertex_table_2d(int32_t *out);
+int ec_vertex_table_3d(int32_t *out);
+/* Exhaustive host check that the per-top-cell closed forms the fast kernels
+ * evaluate equal the per-vertex tables regrouped by entering cell, over all
+ * 2^8 (2D) and 2^26 (3D) neighbour precedence patterns.  Returns the number
+ * of mismatching patterns (0 = consistent). */
+int64_t ec_selfcheck_rules(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EC_H */

@@ -1,0 +1,336 @@
+// ec_api.cu -- C ABI: contexts, argument validation, curve requests.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ec_internal.h"
+#include "ec_rules.h"
+
+namespace ec {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+void clear_error() { g_err.clear(); }
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    return EC_ERR_CUDA;
+}
+
+const Table2D &host_table_2d();
+const Table3D &host_table_3d();
+
+}  // namespace ec
+
+using namespace ec;
+
+struct ec_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int algo = ALGO_AUTO;
+    int validate = 0;
+    int tile_z = 0;
+    int grid = 0;
+    void *ws = nullptr;        // device scratch: [flags 256 B][int64 histogram]
+    size_t ws_bytes = 0;
+    int *host_flag = nullptr;  // pinned, for validation read-back
+    std::mutex mu;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+constexpr size_t kFlagBytes = 256;
+
+int ensure_ws(ec_ctx *ctx, size_t bytes)
+{
+    if (ctx->ws_bytes >= bytes) return EC_OK;
+    if (ctx->ws) {
+        EC_CUDA(cudaDeviceSynchronize());   // the old buffer may still be in use by queued work
+        EC_CUDA(cudaFree(ctx->ws));
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    cudaError_t e = cudaMalloc(&ctx->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cannot allocate %zu bytes of scratch: %s", want, cudaGetErrorString(e));
+        return EC_ERR_OOM;
+    }
+    ctx->ws_bytes = want;
+    return EC_OK;
+}
+
+int validate_common(int ndim, const void *field, const int64_t *dims, int dtype, const void *thr, int32_t L,
+                    int connectivity, uint32_t descriptors, const int64_t *out)
+{
+    if (dtype != EC_U8 && dtype != EC_U16 && dtype != EC_F32) {
+        set_error("unknown dtype %d", dtype);
+        return EC_ERR_DTYPE;
+    }
+    if (dtype == EC_F32 && !thr && L > 0) {
+        set_error("float32 fields need thresholds");
+        return EC_ERR_DTYPE;
+    }
+    if (!dims) { set_error("dims is NULL"); return EC_ERR_ARG; }
+    for (int i = 0; i < ndim; i++)
+        if (dims[i] < 1) { set_error("dims[%d] = %lld < 1", i, (long long)dims[i]); return EC_ERR_ARG; }
+    if (L < 0 || L > 65535) { set_error("L = %d outside [0, 65535]", L); return EC_ERR_ARG; }
+    const uint32_t allowed = ndim == 2 ? 0x7u : 0xFu;
+    if (descriptors == 0 || (descriptors & ~allowed)) {
+        set_error("descriptors 0x%x not valid for %dD", descriptors, ndim);
+        return EC_ERR_ARG;
+    }
+    if (ndim == 2 && connectivity != 8 && connectivity != 4) {
+        set_error("2D connectivity must be 8 or 4 (got %d)", connectivity);
+        return EC_ERR_ARG;
+    }
+    if (ndim == 3) {
+        if (connectivity == 6) {
+            set_error("3D 6-connectivity is not implemented (the paper fixes 26)");
+            return EC_ERR_UNSUPPORTED;
+        }
+        if (connectivity != 26) { set_error("3D connectivity must be 26 (got %d)", connectivity); return EC_ERR_ARG; }
+    }
+    if (L > 0 && (!field || !out)) { set_error("field or out is NULL"); return EC_ERR_ARG; }
+    return EC_OK;
+}
+
+int64_t numel(int ndim, const int64_t *dims)
+{
+    int64_t n = 1;
+    for (int i = 0; i < ndim; i++) n *= dims[i];
+    return n;
+}
+
+int run_curve(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int dtype, const void *thr,
+              int32_t L, int connectivity, uint32_t descriptors, int64_t *out, cudaStream_t s)
+{
+    int rc = validate_common(ndim, field, dims, dtype, thr, L, connectivity, descriptors, out);
+    if (rc) return rc;
+    if (L == 0) return EC_OK;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    const RowMap rows = row_map(descriptors);
+    const size_t hist_bytes = (size_t)rows.nd * L * sizeof(long long);
+    rc = ensure_ws(ctx, kFlagBytes + hist_bytes);
+    if (rc) return rc;
+    int *flags = (int *)ctx->ws;
+    long long *hist = (long long *)((char *)ctx->ws + kFlagBytes);
+    EC_CUDA(cudaMemsetAsync(ctx->ws, 0, kFlagBytes + hist_bytes, s));
+    if (ctx->validate && thr) {
+        rc = launch_check_sorted(thr, dtype, L, flags + 1, s);
+        if (rc) return rc;
+        EC_CUDA(cudaMemcpyAsync(ctx->host_flag, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        EC_CUDA(cudaStreamSynchronize(s));
+        if (*ctx->host_flag) { set_error("thresholds are not non-decreasing"); return EC_ERR_ARG; }
+    }
+    const int algo = ctx->algo == ALGO_VERTEX ? ALGO_VERTEX : ALGO_VOXEL;
+    BinArgs ba{L, dtype, thr};
+    HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0};
+    if (ndim == 3) rc = launch_curve_3d(field, dims, ba, ha, algo, ctx->tile_z, ctx->grid, ctx->num_sms, s);
+    else rc = launch_curve_2d(field, dims, ba, ha, connectivity, algo, ctx->grid, ctx->num_sms, s);
+    if (rc) return rc;
+    int32_t scale[kMaxDesc];
+    row_scales(ndim, algo, descriptors, scale);
+    rc = launch_scan(hist, rows.nd, L, scale, out, flags, s);
+    if (rc) return rc;
+    if (ctx->validate) {
+        EC_CUDA(cudaMemcpyAsync(ctx->host_flag, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+        EC_CUDA(cudaStreamSynchronize(s));
+        if (*ctx->host_flag) { set_error("histogram did not divide by its scale"); return EC_ERR_OVERFLOW; }
+    }
+    return EC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ec_last_error(void) { return g_err.c_str(); }
+
+int ec_ctx_create(ec_ctx **out, int device)
+{
+    clear_error();
+    if (!out) { set_error("ctx is NULL"); return EC_ERR_ARG; }
+    int ndev = 0;
+    EC_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) { set_error("device %d not present (%d devices)", device, ndev); return EC_ERR_ARG; }
+    ec_ctx *ctx = new ec_ctx();
+    ctx->device = device;
+    DeviceGuard dg(device);
+    cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_flag, sizeof(int) * 4);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return cuda_fail(e, "ec_ctx_create");
+    }
+    *out = ctx;
+    return EC_OK;
+}
+
+int ec_ctx_destroy(ec_ctx *ctx)
+{
+    clear_error();
+    if (!ctx) return EC_OK;
+    {
+        DeviceGuard dg(ctx->device);
+        cudaDeviceSynchronize();
+        if (ctx->ws) cudaFree(ctx->ws);
+        if (ctx->host_flag) cudaFreeHost(ctx->host_flag);
+    }
+    delete ctx;
+    return EC_OK;
+}
+
+int ec_ctx_set_option(ec_ctx *ctx, int option, int64_t value)
+{
+    clear_error();
+    if (!ctx) { set_error("ctx is NULL"); return EC_ERR_ARG; }
+    switch (option) {
+    case EC_OPT_ALGO:
+        if (value < 0 || value > 2) { set_error("bad algo %lld", (long long)value); return EC_ERR_ARG; }
+        ctx->algo = (int)value;
+        return EC_OK;
+    case EC_OPT_VALIDATE: ctx->validate = value ? 1 : 0; return EC_OK;
+    case EC_OPT_TILE_Z:
+        if (value < 0 || value > 4096) { set_error("bad tile_z"); return EC_ERR_ARG; }
+        ctx->tile_z = (int)value;
+        return EC_OK;
+    case EC_OPT_GRID:
+        if (value < 0 || value > (1 << 20)) { set_error("bad grid"); return EC_ERR_ARG; }
+        ctx->grid = (int)value;
+        return EC_OK;
+    }
+    set_error("unknown option %d", option);
+    return EC_ERR_ARG;
+}
+
+int ec_curve_2d(ec_ctx *ctx, const void *field_dev, const int64_t dims[2], int dtype, const void *thresholds_dev,
+                int32_t L, int connectivity, uint32_t descriptors, int64_t *out_dev, void *stream)
+{
+    clear_error();
+    if (!ctx) { set_error("ctx is NULL"); return EC_ERR_ARG; }
+    return run_curve(ctx, 2, field_dev, dims, dtype, thresholds_dev, L, connectivity, descriptors, out_dev,
+                     (cudaStream_t)stream);
+}
+
+int ec_curve_3d(ec_ctx *ctx, const void *field_dev, const int64_t dims[3], int dtype, const void *thresholds_dev,
+                int32_t L, int connectivity, uint32_t descriptors, int64_t *out_dev, void *stream)
+{
+    clear_error();
+    if (!ctx) { set_error("ctx is NULL"); return EC_ERR_ARG; }
+    return run_curve(ctx, 3, field_dev, dims, dtype, thresholds_dev, L, connectivity, descriptors, out_dev,
+                     (cudaStream_t)stream);
+}
+
+size_t ec_workspace_bytes(int dtype, int32_t ndim, const int64_t *dims, int32_t L, uint32_t descriptors)
+{
+    (void)dtype; (void)ndim; (void)dims;
+    const RowMap rows = row_map(descriptors);
+    return kFlagBytes + (size_t)rows.nd * (size_t)(L > 0 ? L : 0) * sizeof(long long);
+}
+
+int ec_vertex_table_2d(int32_t *out)
+{
+    if (!out) return EC_ERR_ARG;
+    memcpy(out, host_table_2d().v, sizeof(host_table_2d().v));
+    return EC_OK;
+}
+
+int ec_vertex_table_3d(int32_t *out)
+{
+    if (!out) return EC_ERR_ARG;
+    memcpy(out, host_table_3d().v, sizeof(host_table_3d().v));
+    return EC_OK;
+}
+
+int64_t ec_selfcheck_rules(void)
+{
+    const Table2D &t2 = host_table_2d();
+    const Table3D &t3 = host_table_3d();
+    int64_t bad = 0;
+    // 2D: all 2^8 precedence patterns of the 8 neighbours
+    for (uint32_t i = 0; i < 256; i++) {
+        const uint32_t P = (i & 0xFu) | ((i >> 4) << 5);
+        int sum[4] = {0, 0, 0, 0};
+        for (int v = 0; v < 4; v++) {
+            const int vx = v & 1, vy = v >> 1;
+            unsigned m = 0, cbit = 0;
+            for (int o = 0; o < 4; o++) {
+                const int ox = o & 1, oy = o >> 1;
+                const int pos = (vx + ox) + 3 * (vy + oy);
+                if (pos == 4) cbit = (unsigned)o;
+                else if (P >> pos & 1u) m |= 1u << o;
+            }
+            for (int k = 0; k < 4; k++) sum[k] += t2.v[m | (1u << cbit)][k] - t2.v[m][k];
+        }
+        const Delta2 d = pixel_delta_2d(P);
+        if (sum[0] != 4 * d.ec8 || sum[1] != 4 * d.ec4 || sum[2] != 2 * d.per || sum[3] != 4) bad++;
+    }
+    // 3D: all 2^26 precedence patterns, split across threads
+    unsigned nthr = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<int64_t> part(nthr, 0);
+    std::vector<std::thread> th;
+    const uint32_t total = 1u << 26;
+    for (unsigned t = 0; t < nthr; t++) {
+        th.emplace_back([&, t]() {
+            int64_t b = 0;
+            for (uint32_t i = t; i < total; i += nthr) {
+                const uint32_t P = (i & 0x1FFFu) | ((i >> 13) << 14);
+                int s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+                for (int v = 0; v < 8; v++) {
+                    const int vx = v & 1, vy = (v >> 1) & 1, vz = v >> 2;
+                    const int base = vx + 3 * vy + 9 * vz;
+                    const uint32_t q = P >> base;
+                    const unsigned m = (q & 3u) | (((q >> 3) & 3u) << 2) | (((q >> 9) & 3u) << 4) |
+                                       (((q >> 12) & 3u) << 6);
+                    const unsigned cbit = (unsigned)((1 - vx) + 2 * (1 - vy) + 4 * (1 - vz));
+                    const unsigned mc = m | (1u << cbit);
+                    s0 += t3.v[mc][0] - t3.v[m][0];
+                    s1 += t3.v[mc][1] - t3.v[m][1];
+                    s2 += t3.v[mc][2] - t3.v[m][2];
+                    s3 += t3.v[mc][3] - t3.v[m][3];
+                }
+                const Delta3 d = voxel_delta_3d(P);
+                if (s0 != 8 * d.ec || s1 != 2 * d.per || s2 != 4 * d.area || s3 != 8) b++;
+            }
+            part[t] = b;
+        });
+    }
+    for (auto &x : th) x.join();
+    for (auto v : part) bad += v;
+    return bad;
+}
+
+}  // extern "C"

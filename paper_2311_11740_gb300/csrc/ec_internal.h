@@ -1,0 +1,71 @@
+// ec_internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/ec.h"
+
+namespace ec {
+
+// Thread-local error reporting behind ec_last_error().
+void set_error(const char *fmt, ...);
+void clear_error();
+int cuda_fail(cudaError_t e, const char *what);
+#define EC_CUDA(call)                                               \
+    do {                                                            \
+        cudaError_t _e = (call);                                    \
+        if (_e != cudaSuccess) return ::ec::cuda_fail(_e, #call);   \
+    } while (0)
+
+// Descriptor rows of the output, in the order EC, PERIMETER, AREA, VOLUME.
+constexpr int kMaxDesc = 4;
+struct RowMap {
+    int nd;             // number of output rows
+    int row[kMaxDesc];  // row index for EC, PER, AREA, VOL, or -1
+};
+inline RowMap row_map(uint32_t desc)
+{
+    RowMap r{0, {-1, -1, -1, -1}};
+    for (int i = 0; i < kMaxDesc; i++)
+        if (desc & (1u << i)) r.row[i] = r.nd++;
+    return r;
+}
+
+// Everything a histogram kernel needs to turn a raw value into its level.
+struct BinArgs {
+    int32_t L;          // number of levels; bin L = never active
+    int dtype;          // EC_U8 / EC_U16 / EC_F32
+    const void *thr;    // device thresholds (L values of dtype) or nullptr = identity
+};
+
+// Scratch histogram: int64 [nd][L], zeroed before the kernels run.
+struct HistArgs {
+    RowMap rows;
+    long long *hist;    // global int64 [nd][L]
+    int smem_hist;      // 1: block-private shared-memory int32 histogram, flushed at the end
+};
+
+// Launch helpers implemented in ec_kernels.cu.  All are stream-ordered and
+// return EC_OK or an error status.
+int launch_curve_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha,
+                    int algo, int tile_z, int grid, int num_sms, cudaStream_t s);
+int launch_curve_2d(const void *field, const int64_t dims[2], const BinArgs &ba, const HistArgs &ha,
+                    int connectivity, int algo, int grid, int num_sms, cudaStream_t s);
+// Running sum over levels and exact division by each row's scale.
+int launch_scan(const long long *hist, int nd, int32_t L, const int32_t scale[kMaxDesc],
+                int64_t *out, int *err_flag, cudaStream_t s);
+int launch_check_sorted(const void *thr, int dtype, int32_t L, int *flag, cudaStream_t s);
+
+// Scale of each descriptor row for an algorithm (1 for the per-top-cell path,
+// the table scales for the per-vertex path).
+void row_scales(int ndim, int algo, uint32_t desc, int32_t out[kMaxDesc]);
+
+// Shared-memory budget for the block-private histogram.
+constexpr size_t kSmemHistBudget = 96 * 1024;
+inline bool use_smem_hist(int nd, int32_t L) { return (size_t)nd * (size_t)L * 4 <= kSmemHistBudget; }
+
+enum { ALGO_AUTO = 0, ALGO_VOXEL = 1, ALGO_VERTEX = 2 };
+
+}  // namespace ec

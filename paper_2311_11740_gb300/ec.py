@@ -1,0 +1,310 @@
+"""Python binding of libec (ctypes).  Argument marshalling only: every step of
+the computation runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  If the library is not built, every call raises.
+
+Names follow the C ABI in include/ec.h.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libec.so")
+
+EC_U8, EC_U16, EC_F32 = 0, 1, 2
+EC_DESC_EC, EC_DESC_PERIMETER, EC_DESC_AREA, EC_DESC_VOLUME = 1, 2, 4, 8
+EC_OPT_ALGO, EC_OPT_VALIDATE, EC_OPT_TILE_Z, EC_OPT_GRID = 1, 2, 3, 4
+ALGO_AUTO, ALGO_VOXEL, ALGO_VERTEX = 0, 1, 2
+STATUS = {0: "EC_OK", 1: "EC_ERR_ARG", 2: "EC_ERR_DTYPE", 3: "EC_ERR_UNSUPPORTED", 4: "EC_ERR_OOM",
+          5: "EC_ERR_CUDA", 6: "EC_ERR_TIMEOUT", 7: "EC_ERR_OVERFLOW", 8: "EC_ERR_BUSY"}
+
+
+class ECError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class FieldDesc(ctypes.Structure):
+    _fields_ = [("field", ctypes.c_void_p), ("ndim", ctypes.c_int32), ("dims", ctypes.c_int64 * 3),
+                ("dtype", ctypes.c_int32), ("thresholds", ctypes.c_void_p), ("L", ctypes.c_int32),
+                ("connectivity", ctypes.c_int32), ("descriptors", ctypes.c_uint32),
+                ("out", ctypes.c_void_p)]
+
+
+SLAB_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                           ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded libec.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libec.so is missing ({LIB_PATH}); build it with "
+                                   "paper_2311_11740_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            P, I32, I64, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+            L.ec_last_error.restype = ctypes.c_char_p
+            L.ec_ctx_create.argtypes = [ctypes.POINTER(P), ctypes.c_int]
+            L.ec_ctx_destroy.argtypes = [P]
+            L.ec_ctx_set_option.argtypes = [P, ctypes.c_int, I64]
+            for fn in (L.ec_curve_2d, L.ec_curve_3d):
+                fn.argtypes = [P, P, ctypes.POINTER(I64), ctypes.c_int, P, I32, ctypes.c_int, U32, P, P]
+            L.ec_curve_3d_stream.argtypes = [P, P, SLAB_FN, P, ctypes.POINTER(I64), ctypes.c_int, P, I32,
+                                             ctypes.c_int, U32, I64, ctypes.c_size_t, P]
+            L.ec_batch.argtypes = [P, ctypes.POINTER(FieldDesc), I32, P]
+            L.ec_workspace_bytes.argtypes = [ctypes.c_int, I32, ctypes.POINTER(I64), I32, U32]
+            L.ec_workspace_bytes.restype = ctypes.c_size_t
+            L.ec_vertex_table_2d.argtypes = [P]
+            L.ec_vertex_table_3d.argtypes = [P]
+            L.ec_selfcheck_rules.restype = I64
+            L.ec_server_create.argtypes = [P, ctypes.c_size_t, I32, ctypes.POINTER(P)]
+            L.ec_server_submit.argtypes = [P, ctypes.POINTER(FieldDesc), ctypes.POINTER(ctypes.c_uint64)]
+            L.ec_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int32)]
+            L.ec_server_wait.argtypes = [P, ctypes.c_uint64, I64, ctypes.POINTER(ctypes.c_int32)]
+            L.ec_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+            L.ec_server_destroy.argtypes = [P]
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise ECError(rc, lib().ec_last_error().decode(errors="replace"))
+
+
+def _dims(shape):
+    return (ctypes.c_int64 * len(shape))(*shape)
+
+
+_TORCH_CODES = None
+
+
+def dtype_code(t) -> int:
+    """ec_dtype code of a torch tensor or numpy array."""
+    global _TORCH_CODES
+    if isinstance(t, np.ndarray):
+        return {np.dtype(np.uint8): EC_U8, np.dtype(np.uint16): EC_U16, np.dtype(np.float32): EC_F32}[t.dtype]
+    import torch
+    if _TORCH_CODES is None:
+        _TORCH_CODES = {torch.uint8: EC_U8, torch.uint16: EC_U16, torch.float32: EC_F32}
+    return _TORCH_CODES[t.dtype]
+
+
+def n_rows(descriptors: int) -> int:
+    return bin(descriptors & 0xF).count("1")
+
+
+class Context:
+    """An ec_ctx on one CUDA device (tables, plan cache, scratch)."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(lib().ec_ctx_create(ctypes.byref(h), device))
+        self.handle = h
+
+    def set_option(self, option: int, value: int):
+        _check(lib().ec_ctx_set_option(self.handle, option, int(value)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().ec_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default_ctx = {}
+
+
+def default_context(device: int = 0) -> Context:
+    if device not in _default_ctx:
+        _default_ctx[device] = Context(device)
+    return _default_ctx[device]
+
+
+def _stream_ptr(stream, device):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def curve(field, thresholds=None, L=None, connectivity=None, descriptors=EC_DESC_EC, out=None,
+          ctx: Context | None = None, stream=None):
+    """EC (and other descriptor) curves of a CUDA tensor field (2D or 3D).
+
+    Returns an int64 CUDA tensor [popcount(descriptors), L] (rows EC,
+    perimeter, area, volume).  Calls ec_curve_2d / ec_curve_3d."""
+    import torch
+    assert field.is_cuda and field.is_contiguous(), "field must be a contiguous CUDA tensor"
+    dev = field.device.index if field.device.index is not None else torch.cuda.current_device()
+    ctx = ctx or default_context(dev)
+    if thresholds is not None:
+        assert thresholds.is_cuda and thresholds.dtype == field.dtype and thresholds.is_contiguous()
+        L = thresholds.numel() if L is None else L
+    if L is None:
+        raise ValueError("L is required with identity levels")
+    ndim = field.dim()
+    if connectivity is None:
+        connectivity = 8 if ndim == 2 else 26
+    if out is None:
+        out = torch.empty((n_rows(descriptors), L), dtype=torch.int64, device=field.device)
+    fn = lib().ec_curve_2d if ndim == 2 else lib().ec_curve_3d
+    _check(fn(ctx.handle, ctypes.c_void_p(field.data_ptr()), _dims(field.shape), dtype_code(field),
+              ctypes.c_void_p(thresholds.data_ptr() if thresholds is not None else 0), int(L),
+              int(connectivity), int(descriptors), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream, dev)))
+    return out
+
+
+def curve_3d_stream(field_host=None, producer=None, dims=None, dtype=None, thresholds=None, L=None,
+                    connectivity=26, descriptors=EC_DESC_EC, slab_planes=64, device_mem_cap=0,
+                    ctx: Context | None = None, device: int = 0, user=None):
+    """Low-memory z-slab streaming (ec_curve_3d_stream).  field_host: a host
+    numpy array / CPU tensor (pinned for overlapped copies) or None with a
+    producer callback producer(z0, z1, dst_ptr, stream_ptr) -> int.  Returns a
+    numpy int64 array [rows, L]."""
+    ctx = ctx or default_context(device)
+    if field_host is not None:
+        arr = field_host
+        ptr = arr.data_ptr() if hasattr(arr, "data_ptr") else arr.ctypes.data
+        dims = tuple(arr.shape)
+        dtype = dtype_code(arr)
+    else:
+        ptr = 0
+    thr_ptr = 0
+    thr_keep = None
+    if thresholds is not None:
+        thr_keep = np.ascontiguousarray(thresholds)
+        thr_ptr = thr_keep.ctypes.data
+        L = thr_keep.size if L is None else L
+    out = np.zeros((n_rows(descriptors), L), dtype=np.int64)
+    if producer is not None:
+        cb = SLAB_FN(lambda _u, z0, z1, dst, st: int(producer(z0, z1, dst, st)))
+    else:
+        cb = SLAB_FN()
+    _check(lib().ec_curve_3d_stream(ctx.handle, ctypes.c_void_p(ptr), cb, ctypes.c_void_p(user or 0),
+                                    _dims(dims), int(dtype), ctypes.c_void_p(thr_ptr), int(L),
+                                    int(connectivity), int(descriptors), int(slab_planes),
+                                    ctypes.c_size_t(int(device_mem_cap)), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def _desc(field, thresholds, L, connectivity, descriptors, out) -> FieldDesc:
+    d = FieldDesc()
+    d.field = field.data_ptr() if hasattr(field, "data_ptr") else field.ctypes.data
+    d.ndim = len(field.shape)
+    dims = list(field.shape) + [0] * (3 - len(field.shape))
+    d.dims[:] = dims
+    d.dtype = dtype_code(field)
+    if thresholds is not None:
+        d.thresholds = thresholds.data_ptr() if hasattr(thresholds, "data_ptr") else thresholds.ctypes.data
+    else:
+        d.thresholds = None
+    d.L = int(L)
+    d.connectivity = int(connectivity or (8 if d.ndim == 2 else 26))
+    d.descriptors = int(descriptors)
+    d.out = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+    return d
+
+
+def batch(fields, ctx: Context | None = None, stream=None):
+    """ec_batch over a list of dicts {field, thresholds, L, connectivity,
+    descriptors} with CUDA tensors; returns the list of int64 CUDA outputs."""
+    import torch
+    dev = fields[0]["field"].device.index or 0
+    ctx = ctx or default_context(dev)
+    outs, descs = [], []
+    for f in fields:
+        L = f.get("L") or f["thresholds"].numel()
+        o = torch.empty((n_rows(f.get("descriptors", 1)), L), dtype=torch.int64, device=f["field"].device)
+        outs.append(o)
+        descs.append(_desc(f["field"], f.get("thresholds"), L, f.get("connectivity"), f.get("descriptors", 1), o))
+    arr = (FieldDesc * len(descs))(*descs)
+    _check(lib().ec_batch(ctx.handle, arr, len(descs), _stream_ptr(stream, dev)))
+    return outs
+
+
+class Server:
+    """The continuous-batching request loop (ec_server_*).  Requests use host
+    numpy arrays; outputs are host numpy arrays filled when done."""
+
+    def __init__(self, device_mem_budget: int, max_slots: int = 8, ctx: Context | None = None, device: int = 0):
+        self.ctx = ctx or default_context(device)
+        h = ctypes.c_void_p()
+        _check(lib().ec_server_create(self.ctx.handle, ctypes.c_size_t(int(device_mem_budget)), int(max_slots),
+                                      ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, field, thresholds=None, L=None, connectivity=None, descriptors=EC_DESC_EC):
+        if thresholds is not None:
+            thresholds = np.ascontiguousarray(thresholds, dtype=field.dtype)
+            L = thresholds.size if L is None else L
+        out = np.zeros((n_rows(descriptors), L), dtype=np.int64)
+        d = _desc(field, thresholds, L, connectivity, descriptors, out)
+        t = ctypes.c_uint64()
+        _check(lib().ec_server_submit(self.handle, ctypes.byref(d), ctypes.byref(t)))
+        self._keep[t.value] = (field, thresholds, out)
+        return t.value
+
+    def poll(self, ticket):
+        done, st = ctypes.c_int(), ctypes.c_int32()
+        _check(lib().ec_server_poll(self.handle, ticket, ctypes.byref(done), ctypes.byref(st)))
+        return bool(done.value), st.value
+
+    def wait(self, ticket, timeout_ms: int = 60000):
+        st = ctypes.c_int32()
+        _check(lib().ec_server_wait(self.handle, ticket, int(timeout_ms), ctypes.byref(st)))
+        if st.value != 0:
+            raise ECError(st.value, "request failed")
+        return self._keep[ticket][2]
+
+    def result(self, ticket):
+        return self._keep[ticket][2]
+
+    def stats(self):
+        out = (ctypes.c_double * 5)()
+        _check(lib().ec_server_stats(self.handle, out))
+        return dict(count=out[0], p50_us=out[1], p99_us=out[2], mean_us=out[3], span_us=out[4])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().ec_server_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vertex_table_2d() -> np.ndarray:
+    out = np.zeros((16, 4), np.int32)
+    _check(lib().ec_vertex_table_2d(out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def vertex_table_3d() -> np.ndarray:
+    out = np.zeros((256, 4), np.int32)
+    _check(lib().ec_vertex_table_3d(out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def selfcheck_rules() -> int:
+    return int(lib().ec_selfcheck_rules())

@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA path (through the C ABI) equals the CPU oracle
+element by element.  Curves are integers, so the tolerance is zero."""
+import itertools
+import zlib
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2311_11740_gb300 import ec, workloads
+
+pytestmark = pytest.mark.gpu
+
+ALL2 = ec.EC_DESC_EC | ec.EC_DESC_PERIMETER | ec.EC_DESC_AREA
+ALL3 = ALL2 | ec.EC_DESC_VOLUME
+ALGOS = [ec.ALGO_VOXEL, ec.ALGO_VERTEX]
+
+
+@pytest.fixture(scope="module")
+def ctx(libec):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return ec.Context(0)
+
+
+def to_dev(a):
+    if a is None:
+        return None
+    if a.dtype == np.uint16:
+        return torch.from_numpy(a.astype(np.int32)).cuda().to(torch.uint16)
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_curves(ctx, field, thr, L, conn, desc, algo=ec.ALGO_VOXEL, tile_z=0):
+    ctx.set_option(ec.EC_OPT_ALGO, algo)
+    ctx.set_option(ec.EC_OPT_TILE_Z, tile_z)
+    out = ec.curve(to_dev(field), to_dev(thr), L=L, connectivity=conn, descriptors=desc, ctx=ctx)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def check(ctx, field, thr, L, conn=None, desc=None, algos=ALGOS, tile_z=0):
+    conn = conn or (8 if field.ndim == 2 else 26)
+    desc = desc or (ALL2 if field.ndim == 2 else ALL3)
+    want = oracle.ec_curves(field, thr, L, conn, desc)
+    for algo in algos:
+        got = gpu_curves(ctx, field, thr, L, conn, desc, algo, tile_z)
+        np.testing.assert_array_equal(got, want, err_msg=f"algo={algo} shape={field.shape} L={L}")
+
+
+def test_exhaustive_binary_3x3(ctx):
+    for bits in range(1 << 9):
+        a = np.array([(bits >> i) & 1 for i in range(9)], np.uint8).reshape(3, 3)
+        for conn in (8, 4):
+            check(ctx, a, None, 1, conn=conn)
+
+
+def test_exhaustive_binary_2x2x2(ctx):
+    for bits in range(1 << 8):
+        a = np.array([(bits >> i) & 1 for i in range(8)], np.uint8).reshape(2, 2, 2)
+        check(ctx, a, None, 1)
+
+
+SHAPES3 = [(1, 1, 1), (1, 1, 7), (1, 5, 1), (3, 1, 1), (2, 3, 5), (7, 11, 13), (1, 40, 37), (33, 9, 31),
+           (32, 8, 32), (31, 7, 33), (65, 17, 3), (5, 64, 65), (40, 1, 70)]
+
+
+@pytest.mark.parametrize("shape", SHAPES3)
+@pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
+def test_random_3d(ctx, shape, dtype):
+    rng = np.random.default_rng(zlib.crc32(repr((shape, dtype)).encode()))
+    if dtype == "u8":
+        L = int(rng.integers(1, 40))
+        f = rng.integers(0, L + 3, size=shape).astype(np.uint8)
+        thr = None
+    elif dtype == "u16":
+        L = int(rng.integers(1, 3000))
+        f = rng.integers(0, L + 50, size=shape).astype(np.uint16)
+        thr = None if rng.random() < 0.5 else np.sort(rng.integers(0, L + 60, size=L)).astype(np.uint16)
+    else:
+        L = int(rng.integers(1, 200))
+        f = rng.normal(size=shape).astype(np.float32)
+        thr = np.sort(rng.normal(size=L)).astype(np.float32)
+    check(ctx, f, thr, L)
+
+
+SHAPES2 = [(1, 1), (1, 9), (7, 1), (3, 5), (17, 255), (16, 256), (15, 257), (64, 300), (65, 513), (200, 3)]
+
+
+@pytest.mark.parametrize("shape", SHAPES2)
+@pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
+def test_random_2d(ctx, shape, dtype):
+    rng = np.random.default_rng(zlib.crc32(repr((shape, dtype, 2)).encode()))
+    if dtype == "u8":
+        L = int(rng.integers(1, 256))
+        f = rng.integers(0, 256, size=shape).astype(np.uint8)
+        thr = None if rng.random() < 0.5 else np.sort(rng.integers(0, 256, size=L)).astype(np.uint8)
+    elif dtype == "u16":
+        L = int(rng.integers(1, 5000))
+        f = rng.integers(0, L + 50, size=shape).astype(np.uint16)
+        thr = None
+    else:
+        L = int(rng.integers(1, 300))
+        f = rng.normal(size=shape).astype(np.float32)
+        thr = np.sort(rng.normal(size=L)).astype(np.float32)
+    for conn in (8, 4):
+        check(ctx, f, thr, L, conn=conn)
+
+
+def test_float_special_values(ctx):
+    rng = np.random.default_rng(9)
+    f = rng.normal(size=(9, 10, 11)).astype(np.float32)
+    flat = f.reshape(-1)
+    flat[rng.choice(flat.size, 30, replace=False)] = np.nan
+    flat[rng.choice(flat.size, 10, replace=False)] = np.inf
+    flat[rng.choice(flat.size, 10, replace=False)] = -np.inf
+    flat[rng.choice(flat.size, 10, replace=False)] = -0.0
+    flat[rng.choice(flat.size, 10, replace=False)] = 0.0
+    thr = np.array([-np.inf, -1.0, 0.0, 0.0, 0.0, 0.5, 1.0, 1.0, np.inf], np.float32)
+    check(ctx, f, thr, len(thr))
+    f2 = f[0].copy()
+    check(ctx, f2, thr, len(thr), conn=4)
+
+
+def test_smoothed_3d_and_tile_z(ctx):
+    f, thr = workloads.config3(n=48, nblobs=20, L=97)
+    f, thr = f.numpy(), thr.numpy()
+    for tz in (1, 2, 7, 48, 64):
+        check(ctx, f, thr, len(thr), tile_z=tz)
+
+
+def test_large_level_counts_use_global_paths(ctx):
+    rng = np.random.default_rng(4)
+    # more levels than the shared-memory histogram / threshold copies hold
+    f = rng.integers(0, 65535, size=(6, 20, 30)).astype(np.uint16)
+    check(ctx, f, None, 65535)
+    g = rng.normal(size=(5, 17, 23)).astype(np.float32)
+    thr = np.sort(rng.normal(size=9000)).astype(np.float32)
+    check(ctx, g, thr, len(thr))
+    h = rng.integers(0, 30000, size=(300, 200)).astype(np.uint16)
+    check(ctx, h, None, 30000, conn=4)
+
+
+def test_descriptor_subsets(ctx):
+    f, thr = workloads.config3(n=24, nblobs=6, L=33)
+    f, thr = f.numpy(), thr.numpy()
+    for desc in range(1, 16):
+        check(ctx, f, thr, len(thr), desc=desc)
+    g = workloads.quantize_u8(workloads.grf_2d(3, 40, 50, 2.0)).numpy()
+    for desc in range(1, 8):
+        check(ctx, g, None, 256, desc=desc)
+
+
+def test_config1_full(ctx):
+    f = workloads.config1().numpy()
+    for conn in (8, 4):
+        check(ctx, f, None, 256, conn=conn)
+
+
+def test_argument_errors(ctx):
+    f = torch.zeros((4, 4, 4), dtype=torch.float32, device="cuda")
+    t = torch.zeros(3, dtype=torch.float32, device="cuda")
+    with pytest.raises(ec.ECError) as e:
+        ec.curve(f, t, connectivity=6, ctx=ctx)
+    assert e.value.status == 3
+    with pytest.raises(ec.ECError) as e:
+        ec.curve(f, t, connectivity=8, ctx=ctx)
+    assert e.value.status == 1
+    with pytest.raises(ec.ECError) as e:
+        ec.curve(f[0], t, descriptors=ec.EC_DESC_VOLUME, ctx=ctx)
+    assert e.value.status == 1
+    with pytest.raises(ec.ECError) as e:
+        ec.curve(f, None, L=4, ctx=ctx)
+    assert e.value.status == 2
+    bad = torch.tensor([0.0, 2.0, 1.0], device="cuda")
+    ctx.set_option(ec.EC_OPT_VALIDATE, 1)
+    try:
+        with pytest.raises(ec.ECError) as e:
+            ec.curve(f, bad, ctx=ctx)
+        assert e.value.status == 1
+        ok = ec.curve(f, t, ctx=ctx)
+        torch.cuda.synchronize()
+        assert ok.shape == (1, 3)
+    finally:
+        ctx.set_option(ec.EC_OPT_VALIDATE, 0)
+    # L == 0 is a no-op
+    out = torch.full((1, 1), 7, dtype=torch.int64, device="cuda")
+    ec.lib().ec_curve_3d(ctx.handle, f.data_ptr(), ec._dims(f.shape), ec.EC_F32, t.data_ptr(), 0, 26, 1,
+                         out.data_ptr(), None)
+    torch.cuda.synchronize()
+    assert int(out[0, 0]) == 7
+
+
+@pytest.mark.slow
+def test_config3_full_size(ctx):
+    """The benchmark workload at full size (512^3 float32, 1024 levels, all
+    four descriptors), in the launch configuration the benchmark times."""
+    f, thr = workloads.config3(device="cuda")
+    fh, th = f.cpu().numpy(), thr.cpu().numpy()
+    want = oracle.ec_curves(fh, th, 1024, 26, ALL3)
+    ctx.set_option(ec.EC_OPT_ALGO, ec.ALGO_AUTO)
+    ctx.set_option(ec.EC_OPT_TILE_Z, 0)
+    got = ec.curve(f, thr, descriptors=ALL3, ctx=ctx)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(got.cpu().numpy(), want)
+    # invariants that hold at any size
+    assert want[0, -1] == 1 and want[3, -1] == 512 ** 3
+
+
+@pytest.mark.slow
+def test_config2_full_size(ctx):
+    u8, f32, thr = workloads.config2(device="cuda")
+    want_u8 = oracle.ec_curves(u8.cpu().numpy(), None, 256, 8, ALL2)
+    ctx.set_option(ec.EC_OPT_ALGO, ec.ALGO_AUTO)
+    got = ec.curve(u8, None, L=256, descriptors=ALL2, ctx=ctx)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(got.cpu().numpy(), want_u8)
+    want_f = oracle.ec_curves(f32.cpu().numpy(), thr.cpu().numpy(), 1024, 8, ALL2)
+    got_f = ec.curve(f32, thr, descriptors=ALL2, ctx=ctx)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(got_f.cpu().numpy(), want_f)

@@ -1,0 +1,71 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports
+every function its header declares, and its per-vertex tables reproduce the
+paper's Tables 1 and 2."""
+import os
+import re
+from fractions import Fraction
+
+import numpy as np
+
+from tests import _tables
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(ec_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(libec):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(libec, n), n
+
+
+def test_vertex_table_3d_matches_table2(libec):
+    from paper_2311_11740_gb300 import ec
+    t = ec.vertex_table_3d()
+    full, _ = _tables.table2()
+    for m in range(256):
+        row = full[m]
+        assert Fraction(int(t[m, 0]), 8) == row["EC"], (m, row["row"])
+        assert Fraction(int(t[m, 1]), 2) == row["Perim"], (m, row["row"])
+        assert Fraction(int(t[m, 2]), 4) == row["AreaUsed"], (m, row["row"])
+        assert Fraction(int(t[m, 3]), 8) == row["Volume"], (m, row["row"])
+
+
+def test_vertex_table_2d_matches_table1(libec):
+    from paper_2311_11740_gb300 import ec
+    t = ec.vertex_table_2d()
+    t1 = _tables.table1()
+    for m in range(16):
+        row = t1[m]
+        assert Fraction(int(t[m, 0]), 4) == row["EC8"], m
+        assert Fraction(int(t[m, 1]), 4) == row["EC4"], m
+        assert Fraction(int(t[m, 2]), 2) == row["Perim"], m
+        assert Fraction(int(t[m, 3]), 4) == row["Area"], m
+
+
+def test_regrouped_closed_forms_equal_tables(libec):
+    from paper_2311_11740_gb300 import ec
+    assert ec.selfcheck_rules() == 0
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2311_11740_gb300 import ec
+    monkeypatch.setattr(ec, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(ec, "_lib", None)
+    try:
+        ec.lib()
+    except RuntimeError as e:
+        assert "missing" in str(e)
+    else:
+        raise AssertionError("expected a failure")
