@@ -92,9 +92,16 @@ int ec_ctx_destroy(ec_ctx *ctx);
  *  EC_OPT_VALIDATE: 1 = check device thresholds are non-decreasing (one
  *    stream synchronisation per call; EC_ERR_ARG if not), 0 = trust them.
  *  EC_OPT_TILE_Z: z planes per work item of the 3D kernels (0 = planner).
- *  EC_OPT_GRID: blocks per launch (0 = planner).                           */
-enum { EC_OPT_ALGO = 1, EC_OPT_VALIDATE = 2, EC_OPT_TILE_Z = 3, EC_OPT_GRID = 4 };
+ *  EC_OPT_GRID: blocks per launch (0 = planner).
+ *  EC_OPT_PROFILE: 1 = bracket the main histogram kernel of every request
+ *    with CUDA events on the request's stream (see ec_ctx_profile_read).   */
+enum { EC_OPT_ALGO = 1, EC_OPT_VALIDATE = 2, EC_OPT_TILE_Z = 3, EC_OPT_GRID = 4, EC_OPT_PROFILE = 5 };
 int ec_ctx_set_option(ec_ctx *ctx, int option, int64_t value);
+
+/* Summed device time (ms) and count of the main histogram kernel launches
+ * bracketed since the last read (EC_OPT_PROFILE); waits for the last one to
+ * finish, then resets the count. */
+int ec_ctx_profile_read(ec_ctx *ctx, double *kernel_ms, int64_t *launches);
 
 /* EC / perimeter / area curves of a 2D field resident on the device.
  * field_dev: h*w values of `dtype`; thresholds_dev: L values of `dtype` or
@@ -148,6 +155,21 @@ typedef struct {
  * poorly one at a time).  All pointers in `fields` are device pointers.
  * Results are identical to n separate ec_curve_2d / ec_curve_3d calls. */
 int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, void *stream);
+
+/* ----------------------------------------------------- workload generator
+ * The hash-box field of the low-memory workload (input generation only):
+ * h(x,y,z) = low 16 bits of SplitMix64(seed*2^48 ^ (z mod 2^16)*2^32 ^
+ * (y mod 2^16)*2^16 ^ (x mod 2^16)); v = floor(sum of h over the 5x5x5 box
+ * around (x,y,z) / 2000), in [0, 4095], defined for every integer
+ * coordinate.  ec_gen_hashbox_u16 writes the nz x ny x nx box with origin
+ * (x0, y0, z0) to dst_dev (uint16, C-contiguous) on `stream`.
+ * ec_hashbox_producer is an ec_slab_fn: with user -> ec_hashbox_spec it
+ * writes planes [z0, z1) of the box (relative to spec->z0) for
+ * ec_curve_3d_stream. */
+typedef struct { uint64_t seed; int64_t x0, y0, z0, nx, ny; } ec_hashbox_spec;
+int ec_gen_hashbox_u16(uint64_t seed, int64_t x0, int64_t y0, int64_t z0, int64_t nx, int64_t ny, int64_t nz,
+                       void *dst_dev, void *stream);
+int ec_hashbox_producer(void *user, int64_t z0, int64_t z1, void *dst_dev, void *stream);
 
 /* Bytes of scratch memory ec_curve_2d / ec_curve_3d need for a request. */
 size_t ec_workspace_bytes(int dtype, int32_t ndim, const int64_t *dims, int32_t L,

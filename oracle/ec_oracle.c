@@ -346,17 +346,28 @@ int oracle_hashbox_u16(uint64_t seed, int64_t x0, int64_t y0, int64_t z0,
                        int64_t nx, int64_t ny, int64_t nz, uint16_t *out)
 {
     if (nx < 1 || ny < 1 || nz < 1) return -1;
+    /* the hash of every point of the box grown by 2 on each side, then the
+     * 125-term sum of the definition for every output point */
+    const int64_t px = nx + 4, py = ny + 4, pz = nz + 4;
+    uint16_t *hh = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)(px * py * pz));
+    if (!hh) return -2;
+    #pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < pz; k++)
+        for (int64_t j = 0; j < py; j++)
+            for (int64_t i = 0; i < px; i++)
+                hh[(k * py + j) * px + i] = (uint16_t)hash16(seed, x0 - 2 + i, y0 - 2 + j, z0 - 2 + k);
     #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t k = 0; k < nz; k++)
         for (int64_t j = 0; j < ny; j++)
             for (int64_t i = 0; i < nx; i++) {
                 uint64_t s = 0;
-                for (int dz = -2; dz <= 2; dz++)
-                    for (int dy = -2; dy <= 2; dy++)
-                        for (int dx = -2; dx <= 2; dx++)
-                            s += hash16(seed, x0 + i + dx, y0 + j + dy, z0 + k + dz);
+                for (int dz = 0; dz < 5; dz++)
+                    for (int dy = 0; dy < 5; dy++)
+                        for (int dx = 0; dx < 5; dx++)
+                            s += hh[((k + dz) * py + (j + dy)) * px + (i + dx)];
                 out[(k * ny + j) * nx + i] = (uint16_t)((s * 4096ull) / (125ull * 65536ull));
             }
+    free(hh);
     return 0;
 }
 

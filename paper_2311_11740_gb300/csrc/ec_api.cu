@@ -13,6 +13,7 @@
 
 #include "ec_internal.h"
 #include "ec_rules.h"
+#include "ec_swar.h"
 
 namespace ec {
 
@@ -41,33 +42,7 @@ const Table3D &host_table_3d();
 
 using namespace ec;
 
-struct ec_ctx {
-    int device = 0;
-    int num_sms = 0;
-    int algo = ALGO_AUTO;
-    int validate = 0;
-    int tile_z = 0;
-    int grid = 0;
-    void *ws = nullptr;        // device scratch: [flags 256 B][int64 histogram]
-    size_t ws_bytes = 0;
-    int *host_flag = nullptr;  // pinned, for validation read-back
-    std::mutex mu;
-};
-
 namespace {
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
 constexpr size_t kFlagBytes = 256;
 
@@ -91,7 +66,9 @@ int ensure_ws(ec_ctx *ctx, size_t bytes)
     return EC_OK;
 }
 
-int validate_common(int ndim, const void *field, const int64_t *dims, int dtype, const void *thr, int32_t L,
+}  // namespace
+
+int ec::validate_request(int ndim, const void *field, const int64_t *dims, int dtype, const void *thr, int32_t L,
                     int connectivity, uint32_t descriptors, const int64_t *out)
 {
     if (dtype != EC_U8 && dtype != EC_U16 && dtype != EC_F32) {
@@ -126,6 +103,8 @@ int validate_common(int ndim, const void *field, const int64_t *dims, int dtype,
     return EC_OK;
 }
 
+namespace {
+
 int64_t numel(int ndim, const int64_t *dims)
 {
     int64_t n = 1;
@@ -136,7 +115,7 @@ int64_t numel(int ndim, const int64_t *dims)
 int run_curve(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int dtype, const void *thr,
               int32_t L, int connectivity, uint32_t descriptors, int64_t *out, cudaStream_t s)
 {
-    int rc = validate_common(ndim, field, dims, dtype, thr, L, connectivity, descriptors, out);
+    int rc = validate_request(ndim, field, dims, dtype, thr, L, connectivity, descriptors, out);
     if (rc) return rc;
     if (L == 0) return EC_OK;
     std::lock_guard<std::mutex> lock(ctx->mu);
@@ -158,9 +137,17 @@ int run_curve(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int
     const int algo = ctx->algo == ALGO_VERTEX ? ALGO_VERTEX : ALGO_VOXEL;
     BinArgs ba{L, dtype, thr};
     HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0};
-    if (ndim == 3) rc = launch_curve_3d(field, dims, ba, ha, algo, ctx->tile_z, ctx->grid, ctx->num_sms, s);
+    if (ctx->profile && (rc = prof_begin(ctx, s))) return rc;
+    if (ndim == 3) {
+        rc = EC_ERR_UNSUPPORTED;
+        if (algo == ALGO_VOXEL)
+            rc = launch_fast_3d(field, dims, ba, ha, ctx->tile_z, ctx->grid, ctx->num_sms, flags, s);
+        if (rc == EC_ERR_UNSUPPORTED)
+            rc = launch_curve_3d(field, dims, ba, ha, algo, ctx->tile_z, ctx->grid, ctx->num_sms, s);
+    }
     else rc = launch_curve_2d(field, dims, ba, ha, connectivity, algo, ctx->grid, ctx->num_sms, s);
     if (rc) return rc;
+    if (ctx->profile && (rc = prof_end(ctx, s))) return rc;
     int32_t scale[kMaxDesc];
     row_scales(ndim, algo, descriptors, scale);
     rc = launch_scan(hist, rows.nd, L, scale, out, flags, s);
@@ -168,6 +155,7 @@ int run_curve(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int
     if (ctx->validate) {
         EC_CUDA(cudaMemcpyAsync(ctx->host_flag, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
         EC_CUDA(cudaStreamSynchronize(s));
+        if (*ctx->host_flag & 4) { set_error("a bounded device wait gave up"); return EC_ERR_TIMEOUT; }
         if (*ctx->host_flag) { set_error("histogram did not divide by its scale"); return EC_ERR_OVERFLOW; }
     }
     return EC_OK;
@@ -175,7 +163,47 @@ int run_curve(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int
 
 }  // namespace
 
+int ec::prof_begin(ec_ctx *ctx, cudaStream_t s)
+{
+    if (ctx->prof_used + 2 > ctx->prof_events.size()) {
+        for (int i = 0; i < 256; i++) {
+            cudaEvent_t e;
+            EC_CUDA(cudaEventCreate(&e));
+            ctx->prof_events.push_back(e);
+        }
+    }
+    EC_CUDA(cudaEventRecord(ctx->prof_events[ctx->prof_used], s));
+    return EC_OK;
+}
+
+int ec::prof_end(ec_ctx *ctx, cudaStream_t s)
+{
+    EC_CUDA(cudaEventRecord(ctx->prof_events[ctx->prof_used + 1], s));
+    ctx->prof_used += 2;
+    return EC_OK;
+}
+
 extern "C" {
+
+int ec_ctx_profile_read(ec_ctx *ctx, double *kernel_ms, int64_t *launches)
+{
+    clear_error();
+    if (!ctx || !kernel_ms || !launches) { set_error("NULL argument"); return EC_ERR_ARG; }
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    double tot = 0;
+    for (size_t i = 0; i + 1 < ctx->prof_used; i += 2) {
+        EC_CUDA(cudaEventSynchronize(ctx->prof_events[i + 1]));
+        float ms = 0;
+        EC_CUDA(cudaEventElapsedTime(&ms, ctx->prof_events[i], ctx->prof_events[i + 1]));
+        tot += ms;
+    }
+    *kernel_ms = tot;
+    *launches = (int64_t)(ctx->prof_used / 2);
+    ctx->prof_used = 0;
+    return EC_OK;
+}
+
 
 const char *ec_last_error(void) { return g_err.c_str(); }
 
@@ -208,6 +236,7 @@ int ec_ctx_destroy(ec_ctx *ctx)
         cudaDeviceSynchronize();
         if (ctx->ws) cudaFree(ctx->ws);
         if (ctx->host_flag) cudaFreeHost(ctx->host_flag);
+        for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
     }
     delete ctx;
     return EC_OK;
@@ -231,6 +260,12 @@ int ec_ctx_set_option(ec_ctx *ctx, int option, int64_t value)
         if (value < 0 || value > (1 << 20)) { set_error("bad grid"); return EC_ERR_ARG; }
         ctx->grid = (int)value;
         return EC_OK;
+    case EC_OPT_PROFILE: {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        ctx->profile = value ? 1 : 0;
+        ctx->prof_used = 0;
+        return EC_OK;
+    }
     }
     set_error("unknown option %d", option);
     return EC_ERR_ARG;
@@ -330,6 +365,34 @@ int64_t ec_selfcheck_rules(void)
     }
     for (auto &x : th) x.join();
     for (auto v : part) bad += v;
+    // paired 16-bit-lane evaluation (fast kernel) against the scalar closed form
+    uint64_t rs = 0x9E3779B97F4A7C15ull;
+    auto rnd = [&rs]() {
+        rs ^= rs << 13; rs ^= rs >> 7; rs ^= rs << 17;
+        return rs;
+    };
+    for (int trial = 0; trial < 200000; trial++) {
+        const uint32_t span = (trial % 3 == 0) ? 3u : (trial % 3 == 1 ? 40u : 32767u);
+        uint32_t k0[27], k1[27];
+        for (int i = 0; i < 27; i++) {
+            k0[i] = (uint32_t)(rnd() % span);
+            k1[i] = (uint32_t)(rnd() % span);
+        }
+        uint32_t n[27];
+        for (int i = 0; i < 27; i++) n[i] = k0[i] | (k1[i] << 16);
+        const PairDelta pd = pair_delta<true>(n, n[13]);
+        for (int v = 0; v < 2; v++) {
+            const uint32_t *k = v ? k1 : k0;
+            uint32_t P = 0;
+            for (int i = 0; i < 27; i++) {
+                if (i == 13) continue;
+                const bool prec = i < 13 ? k[i] <= k[13] : k[i] < k[13];
+                P |= (uint32_t)prec << i;
+            }
+            const Delta3 d = voxel_delta_3d(P);
+            if (pd.ec[v] != d.ec || pd.per[v] != d.per || pd.area[v] != d.area) bad++;
+        }
+    }
     return bad;
 }
 

@@ -3,7 +3,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/ec.h"
 
@@ -50,9 +52,16 @@ struct HistArgs {
 // Launch helpers implemented in ec_kernels.cu.  All are stream-ordered and
 // return EC_OK or an error status.
 int launch_curve_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha,
-                    int algo, int tile_z, int grid, int num_sms, cudaStream_t s);
+                    int algo, int tile_z, int grid, int num_sms, cudaStream_t s, const int zrange[4] = nullptr);
 int launch_curve_2d(const void *field, const int64_t dims[2], const BinArgs &ba, const HistArgs &ha,
                     int connectivity, int algo, int grid, int num_sms, cudaStream_t s);
+// The fast per-voxel 3D kernel (TMA staging, paired comparisons).  Returns
+// EC_ERR_UNSUPPORTED without launching when a request does not fit it.
+// zrange (optional): {first, end} planes to count and {first, end} planes
+// that exist in the field; planes of the buffer outside the latter are read
+// as never active (slab halos at the field's ends).
+int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha, int tile_z,
+                   int grid_override, int num_sms, int *err_flag, cudaStream_t s, const int zrange[4] = nullptr);
 // Running sum over levels and exact division by each row's scale.
 int launch_scan(const long long *hist, int nd, int32_t L, const int32_t scale[kMaxDesc],
                 int64_t *out, int *err_flag, cudaStream_t s);
@@ -68,4 +77,44 @@ inline bool use_smem_hist(int nd, int32_t L) { return (size_t)nd * (size_t)L * 4
 
 enum { ALGO_AUTO = 0, ALGO_VOXEL = 1, ALGO_VERTEX = 2 };
 
+// Argument checks shared by every curve entry point.
+int validate_request(int ndim, const void *field, const int64_t *dims, int dtype, const void *thr, int32_t L,
+                     int connectivity, uint32_t descriptors, const int64_t *out);
+
+// Sets the device for a scope and restores the caller's afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace ec
+
+struct ec_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int algo = ec::ALGO_AUTO;
+    int validate = 0;
+    int tile_z = 0;
+    int grid = 0;
+    int profile = 0;
+    void *ws = nullptr;        // device scratch: [flags 256 B][int64 histogram]
+    size_t ws_bytes = 0;
+    int *host_flag = nullptr;  // pinned, for validation read-back
+    std::vector<cudaEvent_t> prof_events;   // start/stop pairs of the main kernel
+    size_t prof_used = 0;
+    std::mutex mu;
+};
+
+namespace ec {
+// Kernel timing (EC_OPT_PROFILE): bracket the main histogram kernel of a request.
+int prof_begin(ec_ctx *ctx, cudaStream_t s);
+int prof_end(ec_ctx *ctx, cudaStream_t s);
 }  // namespace ec

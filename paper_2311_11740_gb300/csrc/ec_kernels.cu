@@ -160,6 +160,8 @@ struct Geom3 {
     int64_t D, H, W;
     int nbx, nby, nbz, tz;   // tile counts and z planes per tile
     int vertex;              // 1: tiles cover the (D+1)(H+1)(W+1) vertex grid
+    int64_t zc0, zc1;        // planes (voxel or vertex) this launch counts
+    int64_t zv0, zv1;        // voxel planes that belong to the field
 };
 
 template <typename T>
@@ -170,7 +172,7 @@ __device__ __forceinline__ void stage_plane3(uint16_t *slot, const T *__restrict
         const int ly = i / RW3, lx = i - ly * RW3;
         const int64_t gx = x0 - 1 + lx, gy = y0 - 1 + ly;
         uint32_t key = (uint32_t)bin.L;
-        if (z >= 0 && z < g.D && gx >= 0 && gx < g.W && gy >= 0 && gy < g.H)
+        if (z >= g.zv0 && z < g.zv1 && gx >= 0 && gx < g.W && gy >= 0 && gy < g.H)
             key = bin(f[(z * g.H + gy) * g.W + gx]);
         slot[i] = (uint16_t)key;
     }
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) k_voxel3d(const T *__restrict__ f, G
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int bx = item % g.nbx, by = (item / g.nbx) % g.nby, bz = item / (g.nbx * g.nby);
         const int64_t x0 = (int64_t)bx * TX3, y0 = (int64_t)by * TY3;
-        const int64_t z0 = (int64_t)bz * g.tz, z1 = min(z0 + g.tz, g.D);
+        const int64_t z0 = g.zc0 + (int64_t)bz * g.tz, z1 = min(z0 + g.tz, g.zc1);
         __syncthreads();   // ring reuse across items
         stage_plane3<T>(ring + ((z0 + 3) & 3) * RS3, f, g, bin, z0 - 1, x0, y0);
         stage_plane3<T>(ring + ((z0 + 4) & 3) * RS3, f, g, bin, z0, x0, y0);
@@ -267,12 +269,11 @@ __global__ void __launch_bounds__(kThreads) k_vertex3d(const T *__restrict__ f, 
     const uint32_t L = (uint32_t)ba.L;
     const int tx = threadIdx.x % TX3, ty = threadIdx.x / TX3;
     const int nitems = g.nbx * g.nby * g.nbz;
-    const int64_t NZ = g.D + 1;
 
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int bx = item % g.nbx, by = (item / g.nbx) % g.nby, bz = item / (g.nbx * g.nby);
         const int64_t x0 = (int64_t)bx * TX3, y0 = (int64_t)by * TY3;
-        const int64_t z0 = (int64_t)bz * g.tz, z1 = min(z0 + g.tz, NZ);
+        const int64_t z0 = g.zc0 + (int64_t)bz * g.tz, z1 = min(z0 + g.tz, g.zc1);
         __syncthreads();
         stage_plane3<T>(ring + ((z0 + 3) & 3) * RS3, f, g, bin, z0 - 1, x0, y0);
         const int64_t X = x0 + tx, Y = y0 + ty;
@@ -452,6 +453,10 @@ __global__ void __launch_bounds__(1024) k_scan(const long long *__restrict__ his
     const long long *h = hist + (size_t)row * L;
     int64_t *o = out + (size_t)row * L;
     const long long scale = sc.s[row];
+    if (*(volatile int *)err & 4) {   // a histogram block gave up a bounded wait: poison the curve
+        for (int k = threadIdx.x; k < L; k += blockDim.x) o[k] = INT64_MIN;
+        return;
+    }
     const int per = (L + blockDim.x - 1) / blockDim.x;
     const int beg = min((int)threadIdx.x * per, L), end = min(beg + per, L);
     long long s = 0;
@@ -520,13 +525,18 @@ static int prepare_kernel(KernelT kernel, size_t smem, int num_sms, int items, i
 
 template <typename T>
 static int launch3(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha,
-                   int algo, int tile_z, int grid_override, int num_sms, cudaStream_t s)
+                   int algo, int tile_z, int grid_override, int num_sms, cudaStream_t s, const int zrange[4])
 {
     Geom3 g;
     g.D = dims[0]; g.H = dims[1]; g.W = dims[2];
     const bool vertex = algo == ALGO_VERTEX;
     g.vertex = vertex ? 1 : 0;
-    const int64_t nx = vertex ? g.W + 1 : g.W, ny = vertex ? g.H + 1 : g.H, nz = vertex ? g.D + 1 : g.D;
+    g.zc0 = zrange ? zrange[0] : 0;
+    g.zc1 = zrange ? zrange[1] : (vertex ? g.D + 1 : g.D);
+    g.zv0 = zrange ? zrange[2] : 0;
+    g.zv1 = zrange ? zrange[3] : g.D;
+    const int64_t nx = vertex ? g.W + 1 : g.W, ny = vertex ? g.H + 1 : g.H, nz = g.zc1 - g.zc0;
+    if (nz < 1) return EC_OK;
     g.tz = tile_z > 0 ? tile_z : 32;
     g.nbx = (int)((nx + TX3 - 1) / TX3);
     g.nby = (int)((ny + TY3 - 1) / TY3);
@@ -551,12 +561,12 @@ static int launch3(const void *field, const int64_t dims[3], const BinArgs &ba, 
 }
 
 int launch_curve_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha,
-                    int algo, int tile_z, int grid, int num_sms, cudaStream_t s)
+                    int algo, int tile_z, int grid, int num_sms, cudaStream_t s, const int zrange[4])
 {
     switch (ba.dtype) {
-    case EC_U8: return launch3<uint8_t>(field, dims, ba, ha, algo, tile_z, grid, num_sms, s);
-    case EC_U16: return launch3<uint16_t>(field, dims, ba, ha, algo, tile_z, grid, num_sms, s);
-    case EC_F32: return launch3<float>(field, dims, ba, ha, algo, tile_z, grid, num_sms, s);
+    case EC_U8: return launch3<uint8_t>(field, dims, ba, ha, algo, tile_z, grid, num_sms, s, zrange);
+    case EC_U16: return launch3<uint16_t>(field, dims, ba, ha, algo, tile_z, grid, num_sms, s, zrange);
+    case EC_F32: return launch3<float>(field, dims, ba, ha, algo, tile_z, grid, num_sms, s, zrange);
     }
     set_error("unknown dtype %d", ba.dtype);
     return EC_ERR_DTYPE;

@@ -2,8 +2,6 @@
 #include "ec_internal.h"
 using namespace ec;
 extern "C" {
-int ec_curve_3d_stream(ec_ctx *, const void *, ec_slab_fn, void *, const int64_t *, int, const void *, int32_t,
-                       int, uint32_t, int64_t, size_t, int64_t *) { set_error("not built yet"); return EC_ERR_UNSUPPORTED; }
 int ec_batch(ec_ctx *, const ec_field_desc *, int32_t, void *) { set_error("not built yet"); return EC_ERR_UNSUPPORTED; }
 int ec_server_create(ec_ctx *, size_t, int32_t, ec_server **) { set_error("not built yet"); return EC_ERR_UNSUPPORTED; }
 int ec_server_submit(ec_server *, const ec_field_desc *, uint64_t *) { return EC_ERR_UNSUPPORTED; }

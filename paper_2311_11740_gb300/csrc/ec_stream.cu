@@ -1,0 +1,149 @@
+// ec_stream.cu -- low-memory 3D processing by z-slabs (Sec. 2.3).
+//
+// The paper's low-memory mode reads only the values a vertex needs straight
+// from the file.  On the GPU the same idea becomes streaming: the field is
+// cut into slabs of S planes; each slab is brought into a device buffer
+// together with one halo plane on each side (a voxel's contribution change
+// depends on its 26 neighbours), while the previous slab is being counted.
+// Every slab adds into one shared int64 histogram, so the result does not
+// depend on the slab height: histograms are additive and every voxel is
+// counted in exactly one slab.  Halo planes that fall outside the field read
+// as never active.
+//
+// Two streams: the side stream fills buffer b (pinned-host copy or the
+// caller's producer), the compute stream waits for it, counts the slab and
+// releases the buffer with an event.  The memory cap bounds the number and
+// height of the buffers.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "ec_internal.h"
+
+using namespace ec;
+
+namespace {
+
+int dtype_size(int dtype) { return dtype == EC_F32 ? 4 : (dtype == EC_U16 ? 2 : 1); }
+
+struct StreamRes {
+    void *mem = nullptr;
+    cudaStream_t comp = nullptr, side = nullptr;
+    cudaEvent_t filled[3] = {nullptr, nullptr, nullptr}, freed[3] = {nullptr, nullptr, nullptr};
+    ~StreamRes()
+    {
+        if (comp) cudaStreamSynchronize(comp);
+        if (side) cudaStreamSynchronize(side);
+        for (int i = 0; i < 3; i++) {
+            if (filled[i]) cudaEventDestroy(filled[i]);
+            if (freed[i]) cudaEventDestroy(freed[i]);
+        }
+        if (comp) cudaStreamDestroy(comp);
+        if (side) cudaStreamDestroy(side);
+        if (mem) cudaFree(mem);
+    }
+};
+
+}  // namespace
+
+extern "C" int ec_curve_3d_stream(ec_ctx *ctx, const void *host_field, ec_slab_fn producer, void *user,
+                                  const int64_t dims[3], int dtype, const void *thresholds_host, int32_t L,
+                                  int connectivity, uint32_t descriptors, int64_t slab_planes, size_t device_mem_cap,
+                                  int64_t *out_host)
+{
+    clear_error();
+    if (!ctx) { set_error("ctx is NULL"); return EC_ERR_ARG; }
+    const void *any_field = host_field ? host_field : (const void *)producer;
+    int rc = validate_request(3, any_field, dims, dtype, thresholds_host, L, connectivity, descriptors, out_host);
+    if (rc) return rc;
+    if (!host_field && !producer) { set_error("need a host field or a producer"); return EC_ERR_ARG; }
+    if (slab_planes < 1) { set_error("slab_planes must be >= 1"); return EC_ERR_ARG; }
+    if (L == 0) return EC_OK;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    DeviceGuard dg(ctx->device);
+
+    const int64_t d = dims[0], h = dims[1], w = dims[2];
+    const int dsz = dtype_size(dtype);
+    const RowMap rows = row_map(descriptors);
+    const size_t plane = (size_t)h * w * dsz;
+    const size_t fixed = 256 + ((size_t)L * dsz + 255) / 256 * 256 + 2 * (size_t)rows.nd * L * sizeof(long long);
+    const int nbuf = 2 + (host_field ? 1 : 0);
+    int64_t S = std::min<int64_t>(slab_planes, d);
+    if (device_mem_cap > 0) {
+        if (device_mem_cap <= fixed) { set_error("memory cap below the fixed scratch (%zu B)", fixed); return EC_ERR_OOM; }
+        const int64_t fit = (int64_t)((device_mem_cap - fixed) / ((size_t)nbuf * plane)) - 2;
+        if (fit < 1) { set_error("memory cap too small for a one-plane slab"); return EC_ERR_OOM; }
+        S = std::min(S, fit);
+    }
+    if (S > INT32_MAX / 4) S = INT32_MAX / 4;
+    const size_t buf_bytes = (size_t)(S + 2) * plane;
+    const size_t total = fixed + (size_t)nbuf * buf_bytes;
+
+    StreamRes res;
+    cudaError_t e = cudaMalloc(&res.mem, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cannot allocate %zu bytes for streaming", total);
+        return EC_ERR_OOM;
+    }
+    char *base = (char *)res.mem;
+    int *flags = (int *)base;
+    void *thr_dev = thresholds_host ? (void *)(base + 256) : nullptr;
+    long long *hist = (long long *)(base + 256 + ((size_t)L * dsz + 255) / 256 * 256);
+    int64_t *out_dev = (int64_t *)(hist + (size_t)rows.nd * L);
+    char *bufs = base + fixed;
+    EC_CUDA(cudaStreamCreateWithFlags(&res.comp, cudaStreamNonBlocking));
+    EC_CUDA(cudaStreamCreateWithFlags(&res.side, cudaStreamNonBlocking));
+    for (int i = 0; i < nbuf; i++) {
+        EC_CUDA(cudaEventCreateWithFlags(&res.filled[i], cudaEventDisableTiming));
+        EC_CUDA(cudaEventCreateWithFlags(&res.freed[i], cudaEventDisableTiming));
+    }
+    EC_CUDA(cudaMemsetAsync(base, 0, fixed, res.comp));
+    if (thresholds_host)
+        EC_CUDA(cudaMemcpyAsync(thr_dev, thresholds_host, (size_t)L * dsz, cudaMemcpyHostToDevice, res.comp));
+    EC_CUDA(cudaStreamSynchronize(res.comp));
+
+    const BinArgs ba{L, dtype, thr_dev};
+    const HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0};
+    const int64_t nslabs = (d + S - 1) / S;
+    for (int64_t i = 0; i < nslabs; i++) {
+        const int b = (int)(i % nbuf);
+        char *buf = bufs + (size_t)b * buf_bytes;
+        const int64_t z0 = i * S, z1 = std::min(z0 + S, d);
+        const int64_t n = z1 - z0;   // planes counted; the buffer holds planes z0-1 .. z1
+        if (i >= nbuf) EC_CUDA(cudaStreamWaitEvent(res.side, res.freed[b], 0));
+        if (host_field) {
+            const int64_t a = std::max<int64_t>(z0 - 1, 0), c = std::min<int64_t>(z1 + 1, d);
+            const char *src = (const char *)host_field + (size_t)a * plane;
+            EC_CUDA(cudaMemcpyAsync(buf + (size_t)(a - (z0 - 1)) * plane, src, (size_t)(c - a) * plane,
+                                    cudaMemcpyHostToDevice, res.side));
+        } else {
+            const int prc = producer(user, z0 - 1, z1 + 1, buf, (void *)res.side);
+            if (prc != 0) { set_error("slab producer failed (%d)", prc); return EC_ERR_ARG; }
+        }
+        EC_CUDA(cudaEventRecord(res.filled[b], res.side));
+        EC_CUDA(cudaStreamWaitEvent(res.comp, res.filled[b], 0));
+        const int64_t bdims[3] = {n + 2, h, w};
+        const int zr[4] = {1, (int)(n + 1), z0 == 0 ? 1 : 0, z1 == d ? (int)(n + 1) : (int)(n + 2)};
+        if (ctx->profile && (rc = prof_begin(ctx, res.comp))) return rc;
+        rc = launch_fast_3d(buf, bdims, ba, ha, ctx->tile_z, ctx->grid, ctx->num_sms, flags, res.comp, zr);
+        if (rc == EC_ERR_UNSUPPORTED)
+            rc = launch_curve_3d(buf, bdims, ba, ha, ALGO_VOXEL, ctx->tile_z, ctx->grid, ctx->num_sms, res.comp, zr);
+        if (rc) return rc;
+        if (ctx->profile && (rc = prof_end(ctx, res.comp))) return rc;
+        EC_CUDA(cudaEventRecord(res.freed[b], res.comp));
+    }
+    int32_t scale[kMaxDesc];
+    row_scales(3, ALGO_VOXEL, descriptors, scale);
+    rc = launch_scan(hist, rows.nd, L, scale, out_dev, flags, res.comp);
+    if (rc) return rc;
+    EC_CUDA(cudaMemcpyAsync(out_host, out_dev, (size_t)rows.nd * L * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            res.comp));
+    int hflags[2] = {0, 0};
+    EC_CUDA(cudaMemcpyAsync(hflags, flags, sizeof hflags, cudaMemcpyDeviceToHost, res.comp));
+    EC_CUDA(cudaStreamSynchronize(res.comp));
+    if (hflags[0] & 4) { set_error("a bounded device wait gave up"); return EC_ERR_TIMEOUT; }
+    return EC_OK;
+}

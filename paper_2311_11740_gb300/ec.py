@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libec.so")
 
 EC_U8, EC_U16, EC_F32 = 0, 1, 2
 EC_DESC_EC, EC_DESC_PERIMETER, EC_DESC_AREA, EC_DESC_VOLUME = 1, 2, 4, 8
-EC_OPT_ALGO, EC_OPT_VALIDATE, EC_OPT_TILE_Z, EC_OPT_GRID = 1, 2, 3, 4
+EC_OPT_ALGO, EC_OPT_VALIDATE, EC_OPT_TILE_Z, EC_OPT_GRID, EC_OPT_PROFILE = 1, 2, 3, 4, 5
 ALGO_AUTO, ALGO_VOXEL, ALGO_VERTEX = 0, 1, 2
 STATUS = {0: "EC_OK", 1: "EC_ERR_ARG", 2: "EC_ERR_DTYPE", 3: "EC_ERR_UNSUPPORTED", 4: "EC_ERR_OOM",
           5: "EC_ERR_CUDA", 6: "EC_ERR_TIMEOUT", 7: "EC_ERR_OVERFLOW", 8: "EC_ERR_BUSY"}
@@ -57,6 +57,7 @@ def lib():
             L.ec_ctx_create.argtypes = [ctypes.POINTER(P), ctypes.c_int]
             L.ec_ctx_destroy.argtypes = [P]
             L.ec_ctx_set_option.argtypes = [P, ctypes.c_int, I64]
+            L.ec_ctx_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)]
             for fn in (L.ec_curve_2d, L.ec_curve_3d):
                 fn.argtypes = [P, P, ctypes.POINTER(I64), ctypes.c_int, P, I32, ctypes.c_int, U32, P, P]
             L.ec_curve_3d_stream.argtypes = [P, P, SLAB_FN, P, ctypes.POINTER(I64), ctypes.c_int, P, I32,
@@ -74,6 +75,7 @@ def lib():
             L.ec_server_wait.argtypes = [P, ctypes.c_uint64, I64, ctypes.POINTER(ctypes.c_int32)]
             L.ec_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
             L.ec_server_destroy.argtypes = [P]
+            L.ec_gen_hashbox_u16.argtypes = [ctypes.c_uint64, I64, I64, I64, I64, I64, I64, P, P]
             _lib = L
     return _lib
 
@@ -116,6 +118,12 @@ class Context:
 
     def set_option(self, option: int, value: int):
         _check(lib().ec_ctx_set_option(self.handle, option, int(value)))
+
+    def profile_read(self):
+        """(summed kernel ms, launches) since the last read (EC_OPT_PROFILE)."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(lib().ec_ctx_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     def close(self):
         if getattr(self, "handle", None):
@@ -292,6 +300,51 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class HashboxSpec(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("x0", ctypes.c_int64), ("y0", ctypes.c_int64), ("z0", ctypes.c_int64),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64)]
+
+
+def gen_hashbox_u16(seed, x0, y0, z0, nx, ny, nz, device=0, stream=None):
+    """The low-memory workload's hash-box field on the device (uint16 tensor
+    (nz, ny, nx)), generated by the library's kernel."""
+    import torch
+    out = torch.empty((nz, ny, nx), dtype=torch.uint16, device=f"cuda:{device}")
+    _check(lib().ec_gen_hashbox_u16(int(seed), int(x0), int(y0), int(z0), int(nx), int(ny), int(nz),
+                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream, device)))
+    return out
+
+
+def hashbox_stream(spec: HashboxSpec, nz: int, thresholds=None, L=4096, descriptors=EC_DESC_EC,
+                   slab_planes=64, device_mem_cap=0, ctx: Context | None = None, device: int = 0, probe=None):
+    """ec_curve_3d_stream over a device-generated hash box (the library's own
+    producer).  probe(z0, z1), if given, is called before each slab."""
+    ctx = ctx or default_context(device)
+    raw = ctypes.cast(lib().ec_hashbox_producer, ctypes.c_void_p).value
+    if probe is None:
+        cb = SLAB_FN(raw)
+        user = ctypes.addressof(spec)
+    else:
+        inner = SLAB_FN(raw)
+
+        def _wrapped(u, z0, z1, dst, st):
+            probe(z0, z1)
+            return inner(u, z0, z1, dst, st)
+        cb = SLAB_FN(_wrapped)
+        user = ctypes.addressof(spec)
+    thr_ptr, thr_keep = 0, None
+    if thresholds is not None:
+        thr_keep = np.ascontiguousarray(thresholds, dtype=np.uint16)
+        thr_ptr = thr_keep.ctypes.data
+        L = thr_keep.size
+    out = np.zeros((n_rows(descriptors), L), dtype=np.int64)
+    dims = (int(nz), int(spec.ny), int(spec.nx))
+    _check(lib().ec_curve_3d_stream(ctx.handle, None, cb, ctypes.c_void_p(user), _dims(dims), EC_U16,
+                                    ctypes.c_void_p(thr_ptr), int(L), 26, int(descriptors), int(slab_planes),
+                                    ctypes.c_size_t(int(device_mem_cap)), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
 
 
 def vertex_table_2d() -> np.ndarray:
