@@ -118,6 +118,25 @@ int ec_curve_3d(ec_ctx *ctx, const void *field_dev, const int64_t dims[3], int d
                 const void *thresholds_dev, int32_t L, int connectivity,
                 uint32_t descriptors, int64_t *out_dev, void *stream);
 
+/* ec_curve_3d for callers that cannot allocate device memory.  The paper has
+ * no counterpart to this entry point.  Who needs it: code whose device memory
+ * is planned by someone else (a framework's caching allocator, a real-time
+ * sensor loop with a fixed budget) and code that must not let an allocation
+ * synchronise the device in the middle of a latency-critical loop.  It takes
+ * no ec_ctx and calls no allocator: its scratch (flags and the int64 level
+ * histogram) is a fixed 512 KiB + 256 B device array inside the library,
+ * held by every GPU that loads the library until the process exits.
+ * Arguments, layout and results are those of ec_curve_3d.  Limits and rules:
+ *  - popcount(descriptors) * L <= 65536 (e.g. all four descriptors with up
+ *    to 16384 levels); larger requests return EC_ERR_ARG.
+ *  - Every call shares that array and clears it first; calls whose work
+ *    overlaps on the GPU (other streams or host threads) race on it and give
+ *    wrong curves, so serialise them.
+ *  - The first call on a device looks up the array's address with that
+ *    device current; make it before any stream capture.                    */
+int ec_curve_3d_noalloc(const void *field_dev, const int64_t dims[3], int dtype, const void *thresholds_dev,
+                        int32_t L, int connectivity, uint32_t descriptors, int64_t *out_dev, void *stream);
+
 /* Low-memory 3D processing (Sec. 2.3 "Low-Memory Processing"): the field is
  * never resident as a whole.  It is processed in z-slabs of `slab_planes`
  * planes plus one halo plane on each side, with at most `device_mem_cap`
