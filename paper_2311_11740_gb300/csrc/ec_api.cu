@@ -120,37 +120,24 @@ int run_curve(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int
     if (L == 0) return EC_OK;
     std::lock_guard<std::mutex> lock(ctx->mu);
     DeviceGuard dg(ctx->device);
-    const RowMap rows = row_map(descriptors);
-    const size_t hist_bytes = (size_t)rows.nd * L * sizeof(long long);
-    rc = ensure_ws(ctx, kFlagBytes + hist_bytes);
+    rc = ensure_ws(ctx, curve_scratch_bytes(descriptors, L));
     if (rc) return rc;
     int *flags = (int *)ctx->ws;
-    long long *hist = (long long *)((char *)ctx->ws + kFlagBytes);
-    EC_CUDA(cudaMemsetAsync(ctx->ws, 0, kFlagBytes + hist_bytes, s));
     if (ctx->validate && thr) {
+        EC_CUDA(cudaMemsetAsync(flags, 0, kFlagBytes, s));
         rc = launch_check_sorted(thr, dtype, L, flags + 1, s);
         if (rc) return rc;
         EC_CUDA(cudaMemcpyAsync(ctx->host_flag, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         EC_CUDA(cudaStreamSynchronize(s));
         if (*ctx->host_flag) { set_error("thresholds are not non-decreasing"); return EC_ERR_ARG; }
     }
-    const int algo = ctx->algo == ALGO_VERTEX ? ALGO_VERTEX : ALGO_VOXEL;
-    BinArgs ba{L, dtype, thr};
-    HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0};
-    if (ctx->profile && (rc = prof_begin(ctx, s))) return rc;
-    if (ndim == 3) {
-        rc = EC_ERR_UNSUPPORTED;
-        if (algo == ALGO_VOXEL)
-            rc = launch_fast_3d(field, dims, ba, ha, ctx->tile_z, ctx->grid, ctx->num_sms, flags, s);
-        if (rc == EC_ERR_UNSUPPORTED)
-            rc = launch_curve_3d(field, dims, ba, ha, algo, ctx->tile_z, ctx->grid, ctx->num_sms, s);
-    }
-    else rc = launch_curve_2d(field, dims, ba, ha, connectivity, algo, ctx->grid, ctx->num_sms, s);
-    if (rc) return rc;
-    if (ctx->profile && (rc = prof_end(ctx, s))) return rc;
-    int32_t scale[kMaxDesc];
-    row_scales(ndim, algo, descriptors, scale);
-    rc = launch_scan(hist, rows.nd, L, scale, out, flags, s);
+    CurvePlan plan;
+    plan.algo = ctx->algo;
+    plan.tile_z = ctx->tile_z;
+    plan.grid = ctx->grid;
+    plan.num_sms = ctx->num_sms;
+    plan.prof = ctx->profile ? ctx : nullptr;
+    rc = enqueue_curve(plan, ndim, field, dims, dtype, thr, L, connectivity, descriptors, out, ctx->ws, s);
     if (rc) return rc;
     if (ctx->validate) {
         EC_CUDA(cudaMemcpyAsync(ctx->host_flag, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -162,6 +149,41 @@ int run_curve(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int
 }
 
 }  // namespace
+
+size_t ec::curve_scratch_bytes(uint32_t descriptors, int32_t L)
+{
+    return kFlagBytes + (size_t)row_map(descriptors).nd * (size_t)(L > 0 ? L : 0) * sizeof(long long);
+}
+
+// Stream-ordered launch sequence of one validated curve request on the given
+// scratch (curve_scratch_bytes): reset, histogram kernel(s), scan.
+int ec::enqueue_curve(const CurvePlan &plan, int ndim, const void *field, const int64_t *dims, int dtype,
+                      const void *thr, int32_t L, int connectivity, uint32_t descriptors, int64_t *out,
+                      void *scratch, cudaStream_t s)
+{
+    const RowMap rows = row_map(descriptors);
+    int *flags = (int *)scratch;
+    long long *hist = (long long *)((char *)scratch + kFlagBytes);
+    EC_CUDA(cudaMemsetAsync(scratch, 0, curve_scratch_bytes(descriptors, L), s));
+    const int algo = plan.algo == ALGO_VERTEX ? ALGO_VERTEX : ALGO_VOXEL;
+    BinArgs ba{L, dtype, thr};
+    HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0};
+    int rc;
+    if (plan.prof && (rc = prof_begin(plan.prof, s))) return rc;
+    if (ndim == 3) {
+        rc = EC_ERR_UNSUPPORTED;
+        if (algo == ALGO_VOXEL) rc = launch_fast_3d(field, dims, ba, ha, plan.tile_z, plan.grid, plan.num_sms, flags, s);
+        if (rc == EC_ERR_UNSUPPORTED)
+            rc = launch_curve_3d(field, dims, ba, ha, algo, plan.tile_z, plan.grid, plan.num_sms, s);
+    } else {
+        rc = launch_curve_2d(field, dims, ba, ha, connectivity, algo, plan.grid, plan.num_sms, s);
+    }
+    if (rc) return rc;
+    if (plan.prof && (rc = prof_end(plan.prof, s))) return rc;
+    int32_t scale[kMaxDesc];
+    row_scales(ndim, algo, descriptors, scale);
+    return launch_scan(hist, rows.nd, L, scale, out, flags, s);
+}
 
 int ec::prof_begin(ec_ctx *ctx, cudaStream_t s)
 {
@@ -292,8 +314,7 @@ int ec_curve_3d(ec_ctx *ctx, const void *field_dev, const int64_t dims[3], int d
 size_t ec_workspace_bytes(int dtype, int32_t ndim, const int64_t *dims, int32_t L, uint32_t descriptors)
 {
     (void)dtype; (void)ndim; (void)dims;
-    const RowMap rows = row_map(descriptors);
-    return kFlagBytes + (size_t)rows.nd * (size_t)(L > 0 ? L : 0) * sizeof(long long);
+    return curve_scratch_bytes(descriptors, L);
 }
 
 int ec_vertex_table_2d(int32_t *out)

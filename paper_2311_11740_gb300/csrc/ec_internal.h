@@ -114,6 +114,20 @@ struct ec_ctx {
 };
 
 namespace ec {
+// How to launch one curve request.
+struct CurvePlan {
+    int algo = ALGO_AUTO;
+    int tile_z = 0;
+    int grid = 0;
+    int num_sms = 1;
+    ec_ctx *prof = nullptr;   // bracket the histogram kernel with this context's events
+};
+// Scratch bytes of one curve request (flags + int64 histogram).
+size_t curve_scratch_bytes(uint32_t descriptors, int32_t L);
+// Enqueue a validated request on `s` using `scratch` (curve_scratch_bytes).
+int enqueue_curve(const CurvePlan &plan, int ndim, const void *field, const int64_t *dims, int dtype,
+                  const void *thr, int32_t L, int connectivity, uint32_t descriptors, int64_t *out, void *scratch,
+                  cudaStream_t s);
 // Kernel timing (EC_OPT_PROFILE): bracket the main histogram kernel of a request.
 int prof_begin(ec_ctx *ctx, cudaStream_t s);
 int prof_end(ec_ctx *ctx, cudaStream_t s);

@@ -220,3 +220,18 @@ def test_config2_full_size(ctx):
     got_f = ec.curve(f32, thr, descriptors=ALL2, ctx=ctx)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(got_f.cpu().numpy(), want_f)
+
+
+@pytest.mark.parametrize("lo,hi,L", [(-0.21, 3.7, 1024), (0.0, 1.0, 256), (-1e3, 5e4, 4000), (1.0, 1.0001, 300)])
+def test_uniform_threshold_binning_edges(ctx, lo, hi, L):
+    """Values exactly on, one ulp below and one ulp above uniform thresholds,
+    plus NaN, infinities and signed zeros: the spacing-based binning must
+    agree with the x <= t_k definition everywhere."""
+    thr = workloads.uniform_thresholds(lo, hi, L).numpy()
+    rng = np.random.default_rng(L)
+    picks = thr[rng.integers(0, L, size=6000)]
+    special = np.array([np.nan] * 50 + [-np.inf, np.inf, -0.0, 0.0, thr[0] - 1, thr[-1] + 1], np.float32)
+    vals = np.concatenate([picks, np.nextafter(picks, np.float32(np.inf)),
+                           np.nextafter(picks, np.float32(-np.inf)), special]).astype(np.float32)
+    f = rng.permutation(np.resize(vals, 24 * 25 * 28)).astype(np.float32).reshape(24, 25, 28)
+    check(ctx, f, thr, L, algos=[ec.ALGO_VOXEL])
