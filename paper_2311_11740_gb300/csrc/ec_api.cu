@@ -46,7 +46,9 @@ namespace {
 
 constexpr size_t kFlagBytes = 256;
 
-int ensure_ws(ec_ctx *ctx, size_t bytes)
+}  // namespace
+
+int ec::ensure_scratch(ec_ctx *ctx, size_t bytes)
 {
     if (ctx->ws_bytes >= bytes) return EC_OK;
     if (ctx->ws) {
@@ -65,8 +67,6 @@ int ensure_ws(ec_ctx *ctx, size_t bytes)
     ctx->ws_bytes = want;
     return EC_OK;
 }
-
-}  // namespace
 
 int ec::validate_request(int ndim, const void *field, const int64_t *dims, int dtype, const void *thr, int32_t L,
                     int connectivity, uint32_t descriptors, const int64_t *out)
@@ -120,7 +120,7 @@ int run_curve(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int
     if (L == 0) return EC_OK;
     std::lock_guard<std::mutex> lock(ctx->mu);
     DeviceGuard dg(ctx->device);
-    rc = ensure_ws(ctx, curve_scratch_bytes(descriptors, L));
+    rc = ensure_scratch(ctx, curve_scratch_bytes(descriptors, L));
     if (rc) return rc;
     int *flags = (int *)ctx->ws;
     if (ctx->validate && thr) {
@@ -259,6 +259,7 @@ int ec_ctx_destroy(ec_ctx *ctx)
         if (ctx->ws) cudaFree(ctx->ws);
         if (ctx->host_flag) cudaFreeHost(ctx->host_flag);
         for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
+        batch_release(ctx);
     }
     delete ctx;
     return EC_OK;

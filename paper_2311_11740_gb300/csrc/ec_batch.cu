@@ -1,0 +1,551 @@
+// ec_batch.cu -- curves of many uneven fields in one persistent launch.
+//
+// Sec. 4 of the paper notes that small images gain little from parallelising
+// one image at a time.  Here every field of a batch is cut into work items
+// (64 x 16 x 64 voxel tiles for 3D fields, 256 x 64 pixel tiles for 2D
+// fields); one persistent kernel pulls items from a global counter, so
+// fields of any size and mix share the whole GPU.  Per item a block:
+//   1. loads the item's field parameters and binning tables into shared
+//      memory (thresholds, byte-value table, uniform-spacing check);
+//   2. walks the tile exactly like the single-field kernels (the 3D path is
+//      the fast paired-comparison code of ec_fast3d.cuh with plain loads);
+//   3. adds its shared-memory histogram into the field's int64 histogram;
+//   4. counts the item as done; the block that completes a field's last item
+//      computes that field's running sums into its output.
+// Nothing waits on another block.  The launch sequence (table upload, reset,
+// kernel) is captured once into a CUDA graph and later calls update and
+// relaunch the instantiated graph.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "ec_fast3d.cuh"
+
+namespace ec {
+
+namespace batch {
+
+using namespace fast3d;
+
+struct BField {
+    const void *field;
+    int64_t dims[3];      // 3D: {D, H, W}; 2D: {1, H, W}
+    const void *thr;
+    long long *hist;      // int64 [nd][L]
+    int64_t *out;
+    int ndim, dtype, L, conn4, nd, nitems;
+    int rows[kMaxDesc];
+    int smem_hist;
+    int done_idx;
+};
+
+struct BItem {
+    int f;
+    int x0, y0, z0, z1;   // 2D: z0..z1 are the item's rows
+};
+
+constexpr int kThrMaxB = 4096;
+
+struct Shared {
+    uint32_t *kring;
+    volatile int *abort_flag;
+    int *sh_hist;          // may be too small for a field: then nullptr for that field
+    size_t hist_cap;       // ints
+    unsigned char *thr;    // thresholds / byte table
+    int *item_bcast;
+};
+
+// Binning tables of a field into shared memory; returns the uniform flag for
+// float32 (1 = the spacing guess is exact for every value).
+__device__ int load_binning(const BField &F, const Shared &S, FBin &fb)
+{
+    const int L = F.L;
+    if (F.dtype == EC_F32) {
+        const float *gt = (const float *)F.thr;
+        const float *t = gt;
+        if (L <= kThrMaxB) {
+            float *s = (float *)S.thr;
+            for (int k = threadIdx.x; k < L; k += blockDim.x) s[k] = gt[k];
+            t = s;
+        }
+        fb.t = t;
+        fb.L = L;
+        fb.t0 = gt[0];
+        fb.tl = gt[L - 1];
+        fb.inv = (L > 1 && fb.tl > fb.t0) ? (float)(L - 1) / (fb.tl - fb.t0) : 0.f;
+        // same interval-end test as k_uniform_check
+        int ok = (fb.t0 == fb.t0 && fb.tl == fb.tl) ? 1 : 0;
+        for (int k = 1 + threadIdx.x; k <= L; k += blockDim.x) {
+            const float lo = gt[k - 1];
+            if (lo != lo) { ok = 0; continue; }
+            if (k == L) {
+                if (lo < INFINITY && bin_guess(nextafterf(lo, INFINITY), fb.t0, fb.inv, L) < L - 1) ok = 0;
+                continue;
+            }
+            const float hi = gt[k];
+            if (hi != hi) { ok = 0; continue; }
+            if (!(lo < hi)) continue;
+            if (bin_guess(nextafterf(lo, INFINITY), fb.t0, fb.inv, L) < k - 1) ok = 0;
+            if (bin_guess(hi, fb.t0, fb.inv, L) > k) ok = 0;
+        }
+        fb.uniform = __syncthreads_and(ok);
+        return fb.uniform;
+    }
+    if (F.dtype == EC_U16) {
+        if (F.thr && L <= kThrMaxB) {
+            uint16_t *s = (uint16_t *)S.thr;
+            const uint16_t *gt = (const uint16_t *)F.thr;
+            for (int k = threadIdx.x; k < L; k += blockDim.x) s[k] = gt[k];
+        }
+    } else {
+        uint16_t *tab = (uint16_t *)S.thr;
+        const uint8_t *gt = (const uint8_t *)F.thr;
+        for (int v = threadIdx.x; v < 256; v += blockDim.x) {
+            uint32_t b;
+            if (!gt) b = v < L ? (uint32_t)v : (uint32_t)L;
+            else {
+                int lo = 0, n = L;
+                while (n > 0) {
+                    const int half = n >> 1;
+                    if (gt[lo + half] < v) { lo += half + 1; n -= half + 1; }
+                    else n = half;
+                }
+                b = (uint32_t)lo;
+            }
+            tab[v] = (uint16_t)b;
+        }
+    }
+    __syncthreads();
+    return 0;
+}
+
+template <typename T>
+__device__ IBin<T> make_ibin(const BField &F, const Shared &S)
+{
+    IBin<T> ib{};
+    ib.L = F.L;
+    if constexpr (sizeof(T) == 1) {
+        ib.table = (const uint16_t *)S.thr;
+    } else {
+        ib.t = (const T *)F.thr;
+        if (F.thr && F.L <= kThrMaxB) ib.t = (const T *)S.thr;
+    }
+    return ib;
+}
+
+template <typename T, bool PER>
+__device__ void item_3d(const BField &F, const BItem &it, const Shared &S, const FBin &fb, int *err)
+{
+    Ctx<T> c;
+    c.p = Params{};
+    c.p.field = F.field;
+    c.p.D = F.dims[0]; c.p.H = F.dims[1]; c.p.W = F.dims[2];
+    c.p.tz = 64;
+    c.p.zc0 = 0; c.p.zc1 = (int)F.dims[0];
+    c.p.zv0 = 0; c.p.zv1 = (int)F.dims[0];
+    c.p.L = F.L;
+    c.p.thr = F.thr;
+    c.p.hist = F.hist;
+    for (int i = 0; i < kMaxDesc; i++) c.p.rows[i] = F.rows[i];
+    c.p.nd = F.nd;
+    c.p.smem_hist = F.smem_hist;
+    c.p.err = err;
+    c.fring = nullptr;
+    c.kring = S.kring;
+    c.bars = nullptr;
+    c.abort_flag = S.abort_flag;
+    c.sh_hist = F.smem_hist ? S.sh_hist : nullptr;
+    c.h64 = nullptr;
+    c.h32 = nullptr;
+    c.fb = fb;
+    c.ib = make_ibin<T>(F, S);
+    c.tr = threadIdx.x >> 4;
+    c.tc = threadIdx.x & 15;
+    c.x0 = it.x0; c.y0 = it.y0; c.z0 = it.z0; c.z1 = it.z1;
+    c.interior = c.x0 >= 4 && c.x0 + TXF + 4 <= c.p.W;
+    c.base = 0;
+    c.parity = 0;
+    uint32_t win[3][3][5];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++)
+#pragma unroll
+            for (int e = 0; e < 5; e++) win[a][b][e] = 0;
+    const int nsteps = c.z1 - c.z0 + 3;
+    for (int t = 0; t < nsteps; t += 3) {
+        zstep<T, false, PER, 0, 0>(c, nullptr, win, t);
+        if (t + 1 < nsteps) zstep<T, false, PER, 1, 0>(c, nullptr, win, t + 1);
+        if (t + 2 < nsteps) zstep<T, false, PER, 2, 0>(c, nullptr, win, t + 2);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t bin2(T v, const FBin &fb, const IBin<T> &ib)
+{
+    if constexpr (sizeof(T) == 4) return fb.uniform ? fbin_uniform(v, fb) : fbin(v, fb);
+    else return ib(v);
+}
+
+// One 2D item: 256 columns of rows [z0, z1), per-pixel regrouped changes.
+template <typename T>
+__device__ void item_2d(const BField &F, const BItem &it, const Shared &S, const FBin &fb)
+{
+    const IBin<T> ib = make_ibin<T>(F, S);
+    const int64_t H = F.dims[1], W = F.dims[2];
+    const T *f = (const T *)F.field;
+    const int L = F.L;
+    uint16_t *ring = (uint16_t *)S.kring;   // 4 rows of 258 keys
+    constexpr int RW = 258;
+    const int tx = threadIdx.x;
+    const int64_t x0 = it.x0;
+    auto stage = [&](int64_t y, int slot) {
+        for (int i = tx; i < RW; i += blockDim.x) {
+            const int64_t gx = x0 - 1 + i;
+            uint32_t key = (uint32_t)L;
+            if (y >= 0 && y < H && gx >= 0 && gx < W) key = bin2<T>(f[y * W + gx], fb, ib);
+            ring[slot * RW + i] = (uint16_t)key;
+        }
+    };
+    const int y0 = it.z0, y1 = it.z1;
+    stage(y0 - 1, (y0 + 3) & 3);
+    stage(y0, (y0 + 4) & 3);
+    int *sh = F.smem_hist ? S.sh_hist : nullptr;
+    for (int y = y0; y < y1; y++) {
+        stage(y + 1, (y + 5) & 3);
+        __syncthreads();
+        const uint16_t *r0 = ring + ((y + 3) & 3) * RW, *r1 = ring + ((y + 4) & 3) * RW,
+                       *r2 = ring + ((y + 5) & 3) * RW;
+        const uint32_t kc = r1[tx + 1];
+        if (x0 + tx < W && kc < (uint32_t)L) {
+            uint32_t P = 0;
+            const uint16_t *rr[3] = {r0, r1, r2};
+#pragma unroll
+            for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+                for (int dx = -1; dx <= 1; dx++) {
+                    if (dx == 0 && dy == 0) continue;
+                    const uint32_t kn = rr[dy + 1][tx + 1 + dx];
+                    const bool lower = dy < 0 || (dy == 0 && dx < 0);
+                    P |= (uint32_t)(lower ? (kn <= kc) : (kn < kc)) << ((dx + 1) + 3 * (dy + 1));
+                }
+            const Delta2 d = pixel_delta_2d(P);
+            const int vals[3] = {F.conn4 ? d.ec4 : d.ec8, d.per, 1};
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                const int r = F.rows[q];
+                if (r < 0 || vals[q] == 0) continue;
+                if (sh) atomicAdd(&sh[r * L + kc], vals[q]);
+                else atomicAdd((unsigned long long *)&F.hist[(size_t)r * L + kc],
+                               (unsigned long long)(long long)vals[q]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Running sums of one field's histogram into its output (one block).
+__device__ void scan_field(const BField &F)
+{
+    __shared__ long long warp_tot[32];
+    const int L = F.L;
+    for (int row = 0; row < F.nd; row++) {
+        const long long *h = F.hist + (size_t)row * L;
+        int64_t *o = F.out + (size_t)row * L;
+        const int per = (L + blockDim.x - 1) / blockDim.x;
+        const int beg = min((int)threadIdx.x * per, L), end = min(beg + per, L);
+        long long s = 0;
+        for (int k = beg; k < end; k++) s += ((volatile const long long *)h)[k];
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        long long incl = s;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += t;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const int nw = blockDim.x >> 5;
+            long long w = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const long long t = __shfl_up_sync(0xffffffffu, w, off);
+                if (lane >= off) w += t;
+            }
+            if (lane < nw) warp_tot[lane] = w;
+        }
+        __syncthreads();
+        long long run = incl - s + (wid > 0 ? warp_tot[wid - 1] : 0);
+        for (int k = beg; k < end; k++) {
+            run += ((volatile const long long *)h)[k];
+            o[k] = run;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+k_batch(const BField *__restrict__ fields, const BItem *__restrict__ items, int nitems, int *counters, int *err,
+        size_t hist_cap)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    Shared S;
+    S.kring = (uint32_t *)smem;
+    S.abort_flag = (volatile int *)(smem + (size_t)NK * KWORDS * 4);
+    S.item_bcast = (int *)(smem + (size_t)NK * KWORDS * 4 + 8);
+    S.sh_hist = (int *)(smem + (size_t)NK * KWORDS * 4 + 16);
+    S.hist_cap = hist_cap;
+    S.thr = (unsigned char *)(S.sh_hist + hist_cap);
+    if (threadIdx.x == 0) *S.abort_flag = 0;
+    int *next_item = counters;          // counters[0]: item counter; counters[1 + f]: items done per field
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) *S.item_bcast = atomicAdd(next_item, 1);
+        __syncthreads();
+        const int i = *S.item_bcast;
+        if (i >= nitems) break;
+        const BItem it = items[i];
+        const BField F = fields[it.f];
+        if (F.smem_hist)
+            for (int k = threadIdx.x; k < F.nd * F.L; k += blockDim.x) S.sh_hist[k] = 0;
+        FBin fb{};
+        load_binning(F, S, fb);   // ends with a barrier
+        if (F.ndim == 3) {
+            const bool per = F.rows[1] >= 0;
+            switch (F.dtype) {
+            case EC_F32: per ? item_3d<float, true>(F, it, S, fb, err) : item_3d<float, false>(F, it, S, fb, err); break;
+            case EC_U16: per ? item_3d<uint16_t, true>(F, it, S, fb, err) : item_3d<uint16_t, false>(F, it, S, fb, err); break;
+            default: per ? item_3d<uint8_t, true>(F, it, S, fb, err) : item_3d<uint8_t, false>(F, it, S, fb, err); break;
+            }
+        } else {
+            switch (F.dtype) {
+            case EC_F32: item_2d<float>(F, it, S, fb); break;
+            case EC_U16: item_2d<uint16_t>(F, it, S, fb); break;
+            default: item_2d<uint8_t>(F, it, S, fb); break;
+            }
+        }
+        __syncthreads();
+        if (F.smem_hist)
+            for (int k = threadIdx.x; k < F.nd * F.L; k += blockDim.x) {
+                const int v = S.sh_hist[k];
+                if (v) atomicAdd((unsigned long long *)&F.hist[k], (unsigned long long)(long long)v);
+            }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) *S.item_bcast = (atomicAdd(&counters[1 + F.done_idx], 1) == F.nitems - 1);
+        __syncthreads();
+        if (*S.item_bcast) {
+            __threadfence();
+            scan_field(F);
+        }
+    }
+}
+
+}  // namespace batch
+
+}  // namespace ec
+
+using namespace ec;
+using namespace ec::batch;
+
+namespace {
+
+struct BatchState {
+    void *dev = nullptr;
+    size_t dev_bytes = 0;
+    void *staging = nullptr;   // pinned
+    size_t staging_bytes = 0;
+    cudaEvent_t staged_free = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+extern "C" int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, void *stream)
+{
+    clear_error();
+    if (!ctx || (n > 0 && !fields) || n < 0) { set_error("bad batch arguments"); return EC_ERR_ARG; }
+    for (int i = 0; i < n; i++) {
+        const ec_field_desc &d = fields[i];
+        if (d.ndim != 2 && d.ndim != 3) { set_error("field %d: ndim must be 2 or 3", i); return EC_ERR_ARG; }
+        const int rc = validate_request(d.ndim, d.field, d.dims, d.dtype, d.thresholds, d.L, d.connectivity,
+                                        d.descriptors, d.out);
+        if (rc) {
+            const std::string msg = ec_last_error();
+            set_error("field %d: %s", i, msg.c_str());
+            return rc;
+        }
+    }
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // ---- host tables: fields (largest first for scheduling) and items
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    auto vox = [&](int i) {
+        const ec_field_desc &d = fields[i];
+        return d.ndim == 3 ? d.dims[0] * d.dims[1] * d.dims[2] : d.dims[0] * d.dims[1];
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return vox(a) > vox(b); });
+    std::vector<BField> bf;
+    std::vector<BItem> items;
+    std::vector<int> separate;   // 3D fields with more levels than 16-bit comparison lanes hold
+    size_t hist_entries = 0, max_smem_entries = 0;
+    for (int oi = 0; oi < n; oi++) {
+        const ec_field_desc &d = fields[order[oi]];
+        if (d.L == 0) continue;
+        if (d.ndim == 3 && d.L > 32767) {
+            separate.push_back(order[oi]);
+            continue;
+        }
+        BField F{};
+        F.field = d.field;
+        F.ndim = d.ndim;
+        F.dtype = d.dtype;
+        F.L = d.L;
+        F.thr = d.thresholds;
+        F.out = d.out;
+        F.conn4 = d.connectivity == 4;
+        const RowMap rm = row_map(d.descriptors);
+        F.nd = rm.nd;
+        for (int k = 0; k < kMaxDesc; k++) F.rows[k] = rm.row[k];
+        F.smem_hist = use_smem_hist(rm.nd, d.L) ? 1 : 0;
+        if (F.smem_hist) max_smem_entries = std::max(max_smem_entries, (size_t)rm.nd * d.L);
+        F.hist = (long long *)(uintptr_t)hist_entries;   // offset, fixed up below
+        hist_entries += (size_t)rm.nd * d.L;
+        F.done_idx = (int)bf.size();
+        const int f = (int)bf.size();
+        int cnt = 0;
+        if (d.ndim == 3) {
+            F.dims[0] = d.dims[0]; F.dims[1] = d.dims[1]; F.dims[2] = d.dims[2];
+            for (int64_t z = 0; z < d.dims[0]; z += 64)
+                for (int64_t y = 0; y < d.dims[1]; y += TYF)
+                    for (int64_t x = 0; x < d.dims[2]; x += TXF) {
+                        items.push_back(BItem{f, (int)x, (int)y, (int)z, (int)std::min<int64_t>(z + 64, d.dims[0])});
+                        cnt++;
+                    }
+        } else {
+            F.dims[0] = 1; F.dims[1] = d.dims[0]; F.dims[2] = d.dims[1];
+            for (int64_t y = 0; y < d.dims[0]; y += 64)
+                for (int64_t x = 0; x < d.dims[1]; x += 256) {
+                    items.push_back(BItem{f, (int)x, 0, (int)y, (int)std::min<int64_t>(y + 64, d.dims[0])});
+                    cnt++;
+                }
+        }
+        F.nitems = cnt;
+        bf.push_back(F);
+    }
+    for (int i : separate) {
+        // one ordinary launch sequence per such field, on the batch's stream
+        const ec_field_desc &d = fields[i];
+        int rc = ensure_scratch(ctx, curve_scratch_bytes(d.descriptors, d.L));
+        if (rc) return rc;
+        CurvePlan plan;
+        plan.algo = ALGO_VOXEL;
+        plan.num_sms = ctx->num_sms;
+        rc = enqueue_curve(plan, 3, d.field, d.dims, d.dtype, d.thresholds, d.L, d.connectivity, d.descriptors, d.out,
+                           ctx->ws, s);
+        if (rc) return rc;
+    }
+    if (bf.empty()) return EC_OK;
+    if (items.size() > (size_t)INT32_MAX) { set_error("batch too large"); return EC_ERR_UNSUPPORTED; }
+
+    // ---- device layout: [flags 256][fields][items][counters][hist]
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t fb_bytes = al(bf.size() * sizeof(BField)), it_bytes = al(items.size() * sizeof(BItem));
+    const size_t ct_bytes = al((bf.size() + 1) * sizeof(int)), hs_bytes = hist_entries * sizeof(long long);
+    const size_t total = 256 + fb_bytes + it_bytes + ct_bytes + hs_bytes;
+    if (!ctx->batch_state) ctx->batch_state = new BatchState();
+    BatchState &st = *(BatchState *)ctx->batch_state;
+    if (st.staged_free) EC_CUDA(cudaEventSynchronize(st.staged_free));   // previous batch done with staging
+    if (st.dev_bytes < total) {
+        if (st.dev) { EC_CUDA(cudaDeviceSynchronize()); cudaFree(st.dev); st.dev = nullptr; }
+        if (st.exec) { cudaGraphExecDestroy(st.exec); st.exec = nullptr; }
+        const size_t want = std::max(total, (size_t)4 << 20);
+        if (cudaMalloc(&st.dev, want) != cudaSuccess) { cudaGetLastError(); set_error("batch scratch allocation failed"); return EC_ERR_OOM; }
+        st.dev_bytes = want;
+    }
+    const size_t table_bytes = fb_bytes + it_bytes;
+    if (st.staging_bytes < table_bytes) {
+        if (st.staging) cudaFreeHost(st.staging);
+        if (st.exec) { cudaGraphExecDestroy(st.exec); st.exec = nullptr; }
+        const size_t want = std::max(table_bytes, (size_t)1 << 20);
+        if (cudaMallocHost(&st.staging, want) != cudaSuccess) { cudaGetLastError(); set_error("batch staging allocation failed"); return EC_ERR_OOM; }
+        st.staging_bytes = want;
+    }
+    if (!st.staged_free) EC_CUDA(cudaEventCreateWithFlags(&st.staged_free, cudaEventDisableTiming));
+    char *base = (char *)st.dev;
+    int *flags = (int *)base;
+    BField *d_fields = (BField *)(base + 256);
+    BItem *d_items = (BItem *)(base + 256 + fb_bytes);
+    int *d_counters = (int *)(base + 256 + fb_bytes + it_bytes);
+    long long *d_hist = (long long *)(base + 256 + fb_bytes + it_bytes + ct_bytes);
+    for (auto &F : bf) F.hist = d_hist + (size_t)(uintptr_t)F.hist;
+    memcpy(st.staging, bf.data(), bf.size() * sizeof(BField));
+    memcpy((char *)st.staging + fb_bytes, items.data(), items.size() * sizeof(BItem));
+
+    // ---- launch configuration
+    const size_t hist_cap = std::max<size_t>(max_smem_entries, 1);
+    const size_t smem = (size_t)NK * KWORDS * 4 + 16 + hist_cap * 4 + (size_t)kThrMaxB * 4;
+    EC_CUDA(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kThreads, smem));
+    if (occ < 1) { set_error("batch kernel does not fit (%zu B shared)", smem); return EC_ERR_UNSUPPORTED; }
+    int grid = ctx->grid > 0 ? ctx->grid : ctx->num_sms * occ;
+    grid = std::min<int>(grid, (int)items.size());
+
+    // ---- capture the sequence into a graph; update the cached executable if possible
+    cudaStream_t cap = nullptr;
+    EC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemcpyAsync(d_fields, st.staging, table_bytes, cudaMemcpyHostToDevice, cap);
+        cudaMemsetAsync(flags, 0, 256, cap);
+        cudaMemsetAsync(d_counters, 0, ct_bytes + hs_bytes, cap);
+        k_batch<<<grid, kThreads, smem, cap>>>(d_fields, d_items, (int)items.size(), d_counters, flags, hist_cap);
+        e = cudaStreamEndCapture(cap, &graph);
+    }
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e, "batch graph capture"); }
+    bool updated = false;
+    if (st.exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(st.exec, graph, &info) == cudaSuccess) updated = true;
+        else {
+            cudaGetLastError();
+            cudaGraphExecDestroy(st.exec);
+            st.exec = nullptr;
+        }
+    }
+    if (!updated) {
+        e = cudaGraphInstantiate(&st.exec, graph, 0);
+        if (e != cudaSuccess) { cudaGraphDestroy(graph); st.exec = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+    }
+    cudaGraphDestroy(graph);
+    if (ctx->profile && prof_begin(ctx, s)) return EC_ERR_CUDA;
+    EC_CUDA(cudaGraphLaunch(st.exec, s));
+    if (ctx->profile && prof_end(ctx, s)) return EC_ERR_CUDA;
+    EC_CUDA(cudaEventRecord(st.staged_free, s));
+    return EC_OK;
+}
+
+// Release the batch state of a context (called by ec_ctx_destroy).
+void ec::batch_release(ec_ctx *ctx)
+{
+    BatchState *st = (BatchState *)ctx->batch_state;
+    if (!st) return;
+    if (st->exec) cudaGraphExecDestroy(st->exec);
+    if (st->staged_free) cudaEventDestroy(st->staged_free);
+    if (st->dev) cudaFree(st->dev);
+    if (st->staging) cudaFreeHost(st->staging);
+    delete st;
+    ctx->batch_state = nullptr;
+}

@@ -163,37 +163,6 @@ struct IBin {
     }
 };
 
-// Decide whether bin_guess is always the true bin or one below it, for every
-// float: the guess is monotone in x, so it suffices to check both ends of
-// every level's interval (t_{k-1}, t_k] and the interval above t_{L-1}.
-// Writes uni[0] (1 = fast path exact) and uni[1] (the scale, float bits).
-__global__ void k_uniform_check(const float *t, int L, int *uni)
-{
-    __shared__ int ok;
-    const float t0 = t[0], tl = t[L - 1];
-    const float inv = (L > 1 && tl > t0) ? (float)(L - 1) / (tl - t0) : 0.f;
-    if (threadIdx.x == 0) ok = (t0 == t0 && tl == tl) ? 1 : 0;
-    __syncthreads();
-    for (int k = 1 + threadIdx.x; k <= L; k += blockDim.x) {
-        const float lo = t[k - 1];
-        if (lo != lo) { ok = 0; continue; }
-        if (k == L) {
-            if (lo < INFINITY && bin_guess(nextafterf(lo, INFINITY), t0, inv, L) < L - 1) ok = 0;
-            continue;
-        }
-        const float hi = t[k];
-        if (hi != hi) { ok = 0; continue; }
-        if (!(lo < hi)) continue;   // empty interval
-        if (bin_guess(nextafterf(lo, INFINITY), t0, inv, L) < k - 1) ok = 0;
-        if (bin_guess(hi, t0, inv, L) > k) ok = 0;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uni[0] = ok;
-        uni[1] = __float_as_int(inv);
-    }
-}
-
 // ----------------------------------------------------------------- kernel
 
 constexpr int FSTRIDE = ((BX * BY * 4 + 127) / 128) * 128 / 4;   // float slot stride (128-byte aligned)

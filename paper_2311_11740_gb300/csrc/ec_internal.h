@@ -110,6 +110,7 @@ struct ec_ctx {
     int *host_flag = nullptr;  // pinned, for validation read-back
     std::vector<cudaEvent_t> prof_events;   // start/stop pairs of the main kernel
     size_t prof_used = 0;
+    void *batch_state = nullptr;            // ec_batch tables, graph and pinned staging
     std::mutex mu;
 };
 
@@ -128,6 +129,10 @@ size_t curve_scratch_bytes(uint32_t descriptors, int32_t L);
 int enqueue_curve(const CurvePlan &plan, int ndim, const void *field, const int64_t *dims, int dtype,
                   const void *thr, int32_t L, int connectivity, uint32_t descriptors, int64_t *out, void *scratch,
                   cudaStream_t s);
+// Grow the context's scratch to at least `bytes` (device-synchronising when it grows).
+int ensure_scratch(ec_ctx *ctx, size_t bytes);
+// Free what ec_batch keeps in a context.
+void batch_release(ec_ctx *ctx);
 // Kernel timing (EC_OPT_PROFILE): bracket the main histogram kernel of a request.
 int prof_begin(ec_ctx *ctx, cudaStream_t s);
 int prof_end(ec_ctx *ctx, cudaStream_t s);
