@@ -1,11 +1,16 @@
 """Benchmark: EC-curve throughput of a 512^3 float32 field with 1024 levels.
 
-One step = one full curve request (EC, perimeter, area and volume) through
-the C ABI: scratch reset, the histogram kernel over every voxel, the scan.
-Inputs are resident in HBM before the timed region (537 MB, larger than L2,
-so no flush is needed between steps).  Prints one JSON line.
+One step = one full curve request (EC, surface area and volume curves)
+through the C ABI: scratch reset, the spacing check of the thresholds, the
+histogram kernel over every voxel, the scan.  Inputs are resident in HBM
+before the timed region (537 MB, larger than L2, so no flush is needed
+between steps).  Prints one JSON line, which also carries the same step with
+all four descriptors, the end-to-end number through the host-buffer call,
+and the batched-versus-per-field comparison on the served request mix.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --profile-case     (the kernel alone on a 256 x 512 x 512
+                                      slab of the field, for ncu captures)
 
 --impl reference times the CPU oracle (the plain cell-counting reference) on
 this machine's host cores, on a bounded sample of the same workload.
@@ -30,13 +35,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "EC-curve Gvoxels/s & % HBM peak (512³ f32, 1024 lvls); batched vs per-field"
 WORKLOAD = ("512^3 float32 density: 2000 Gaussian blobs (r~U[3,12], a~U[0.5,1.5]) + N(0,0.05^2) noise, "
-            "seed 3; 1024 uniform thresholds over [min,max]; EC+perimeter+area+volume curves (int64), "
+            "seed 3; 1024 uniform thresholds over [min,max]; EC, surface-area and volume curves (int64), "
             "26-connectivity")
 N = 512
 L = 1024
-DESC = 15
-KERNEL = "k_voxel3d"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_voxel3d_512cube_f32.json")
+DESC = 13            # EC | AREA | VOLUME
+DESC_ALL = 15        # EC | PERIMETER | AREA | VOLUME
+KERNEL = "k_voxel3d_fast"
+LAUNCHES_PER_STEP = 3   # spacing check, histogram kernel, scan
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_voxel3d_fast_512cube_f32.json")
 
 
 def kernel_source_hash() -> str:
@@ -124,24 +131,100 @@ def traffic_per_launch():
 
 
 def cpu_baseline(field_cpu, thr_cpu, budget_s: float):
-    """Time the oracle (as it stands) on a z-slab sample of the workload."""
+    """Time the oracle (as it stands) on a bounded sample of the workload:
+    whole passes over the field (or over its first z-planes when one pass
+    would exceed the budget), repeated until about `budget_s` seconds."""
     import numpy as np
     import oracle
     thr = thr_cpu.numpy()
-    # calibrate on 4 planes, then size the sample to the budget
     probe = np.ascontiguousarray(field_cpu[:4].numpy())
     t0 = time.perf_counter()
     oracle.ec_curves(probe, thr, L, 26, DESC)
     per_plane = (time.perf_counter() - t0) / 4
-    planes = int(max(4, min(N, budget_s / max(per_plane, 1e-6))))
+    planes = int(max(4, min(field_cpu.shape[0], budget_s / max(per_plane, 1e-6))))
     sample = np.ascontiguousarray(field_cpu[:planes].numpy())
-    t0 = time.perf_counter()
-    oracle.ec_curves(sample, thr, L, 26, DESC)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.ec_curves(sample, thr, L, 26, DESC)
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
     dt = time.perf_counter() - t0
-    vox = sample.size
+    vox = sample.size * reps
     return {"value": vox / dt / 1e9, "unit": "Gvoxels/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"first {planes} z-planes ({planes}x512x512 = {vox} voxels) of the same field and "
-                      f"thresholds, all four descriptors, {dt:.2f} s"}
+            "sample": f"{reps} pass(es) over the first {planes} z-planes ({sample.size} voxels each) of the same "
+                      f"field and thresholds, EC+area+volume, {dt:.1f} s"}
+
+
+def time_device(fn, steps):
+    import torch
+    stream = torch.cuda.current_stream()
+    st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    st.record(stream)
+    for _ in range(steps):
+        fn()
+    en.record(stream)
+    torch.cuda.synchronize()
+    return st.elapsed_time(en) / steps
+
+
+def batched_vs_per_field(ec, ctx, n_requests, seed=5):
+    """The served workload's mix (70 % 2D uint8, 30 % 3D float32, uneven
+    sizes and level counts): one launch per field, one batched persistent
+    launch, and the continuous-admission server fed with Poisson arrivals."""
+    import numpy as np
+    import torch
+    from paper_2311_11740_gb300 import workloads
+    reqs = workloads.request_stream(seed=seed, n=n_requests, max_2d=2048, max_3d=256)
+    fields, cells = [], 0
+    for r in reqs:
+        f, thr = workloads.request_field(r, device="cuda")
+        fields.append(dict(field=f, thresholds=thr, L=r["L"], descriptors=7 if r["ndim"] == 2 else 15))
+        cells += f.numel()
+    outs = [ec.curve(d["field"], d["thresholds"], L=d["L"], descriptors=d["descriptors"], ctx=ctx) for d in fields]
+    ec.batch(fields, ctx=ctx)
+    per_ms = time_device(lambda: [ec.curve(d["field"], d["thresholds"], L=d["L"], descriptors=d["descriptors"],
+                                           ctx=ctx, out=o) for d, o in zip(fields, outs)], 3)
+    bat_ms = time_device(lambda: ec.batch(fields, ctx=ctx), 5)
+    same = all(torch.equal(a, b) for a, b in zip(outs, ec.batch(fields, ctx=ctx)))
+    # served: page-locked host fields; first a closed-loop pass (everything
+    # submitted at once) gives the server's capacity, then Poisson arrivals at
+    # 0.9 of that capacity give the latency distribution
+    host = [(d["field"].cpu().pin_memory(), None if d["thresholds"] is None else d["thresholds"].cpu().numpy(),
+             d["L"], d["descriptors"]) for d in fields]
+    want = [o.cpu().numpy() for o in outs]
+    sv = ec.Server(device_mem_budget=8 << 30, max_slots=8, ctx=ctx)
+    t0 = time.perf_counter()
+    tickets = [sv.submit(f, thr, L=Lr, descriptors=dsc) for f, thr, Lr, dsc in host]
+    served_ok = all(np.array_equal(sv.wait(t, 600000), w) for t, w in zip(tickets, want))
+    cap_s = time.perf_counter() - t0
+    sv.close()
+    rate = 0.9 * len(host) / cap_s
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=len(host))
+    sv = ec.Server(device_mem_budget=8 << 30, max_slots=8, ctx=ctx)
+    t0 = time.perf_counter()
+    due = t0
+    tickets = []
+    for (f, thr, Lr, dsc), g in zip(host, gaps):
+        due += g
+        while time.perf_counter() < due:
+            pass
+        tickets.append(sv.submit(f, thr, L=Lr, descriptors=dsc))
+    served_ok &= all(np.array_equal(sv.wait(t, 600000), w) for t, w in zip(tickets, want))
+    span = time.perf_counter() - t0
+    stats = sv.stats()
+    sv.close()
+    return {"workload": f"{len(fields)} requests, seed {seed}: 70% 2D uint8 (side log-uniform 64..2048, 256 levels), "
+                        f"30% 3D float32 (side log-uniform 32..256, 64..1024 levels), smoothed GRFs",
+            "cells": cells, "per_field_gcells_s": cells / per_ms / 1e6, "batched_gcells_s": cells / bat_ms / 1e6,
+            "per_field_ms": per_ms, "batched_ms": bat_ms, "identical": bool(same and served_ok),
+            "served": {"closed_loop_gcells_s_incl_h2d": cells / cap_s / 1e9,
+                       "offered_rate_req_s": rate, "offered_load": 0.9,
+                       "gcells_s_incl_h2d": cells / span / 1e9,
+                       "p50_us": stats["p50_us"], "p99_us": stats["p99_us"], "slots": 8,
+                       "host_fields": "page-locked"}}
 
 
 def run_reference(args):
@@ -191,6 +274,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", type=int, default=0, help="testing only: edge of a smaller cube")
+    ap.add_argument("--batch-requests", type=int, default=256)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run two curve requests on the first 256 planes of the field and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -210,10 +297,19 @@ def main():
 
     n = args.small or N
     field, thr = workloads.config3(device="cuda", n=n) if args.small else workloads.config3(device="cuda")
+    if args.profile_case:
+        slab = field[:256].contiguous()
+        ctx = ec.Context(local)
+        for _ in range(2):
+            res = ec.curve(slab, thr, descriptors=DESC, ctx=ctx)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "256x512x512 float32 slab of the benchmark field, EC+area+volume",
+                          "volume_at_top": int(res[2, -1])}))
+        return 0
     vox = field.numel()
     ctx = ec.Context(local)
     ctx.set_option(ec.EC_OPT_PROFILE, 1)
-    out = torch.empty((4, L), dtype=torch.int64, device="cuda")
+    out = torch.empty((3, L), dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         ec.curve(field, thr, descriptors=DESC, out=out, ctx=ctx)
@@ -259,6 +355,13 @@ def main():
                "h2d_bytes_per_step": int(host.numel() * 4 + thr_h.nbytes),
                "d2h_bytes_per_step": int(res.nbytes)}
 
+    # the same step with all four descriptors (perimeter included)
+    out_all = torch.empty((4, L), dtype=torch.int64, device="cuda")
+    ec.curve(field, thr, descriptors=DESC_ALL, out=out_all, ctx=ctx)
+    all_ms = time_device(lambda: ec.curve(field, thr, descriptors=DESC_ALL, out=out_all, ctx=ctx), 50)
+    ctx.profile_read()
+    batched = None if (args.no_batch or rank != 0) else batched_vs_per_field(ec, ctx, args.batch_requests)
+
     if rank != 0:
         return 0
     peak, peak_kind = measured_peaks()
@@ -272,13 +375,16 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if not args.small else f"{n}^3 test cube", "field_bytes": vox * 4,
                    "l2": "inputs larger than L2 (537 MB field), no flush",
-                   "per_step": "memset + k_voxel3d + k_scan through ec_curve_3d"},
+                   "per_step": "ec_curve_3d: memset + k_uniform_check + k_voxel3d_fast + k_scan"},
         "roofline": {"bound": "hbm", "kernel": KERNEL, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
                      "kernel_avg_us": kernel_avg_s * 1e6, "algorithmic_bytes_per_launch": bytes_per_launch},
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clocks,
+        "all_descriptors": {"descriptors": "EC+perimeter+area+volume", "ms_per_step": all_ms,
+                            "value": vox / all_ms / 1e6, "unit": "Gvoxels/s"},
+        "batched_vs_per_field": batched,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(field.cpu(), thr.cpu(), args.cpu_budget)

@@ -48,6 +48,7 @@ def _load():
             lib.oracle_bin.argtypes = [P, I64, ctypes.c_int, P, I32, P]
             lib.oracle_curves_2d.argtypes = [P, I64, I64, I32, P, P, P, P]
             lib.oracle_curves_3d.argtypes = [P, I64, I64, I64, I32, P, P, P, P]
+            lib.oracle_curves_3d_zrange.argtypes = [P, I64, I64, I64, I32, I64, I64, P, P, P, P]
             lib.oracle_hashbox_u16.argtypes = [ctypes.c_uint64, I64, I64, I64, I64, I64, I64, P]
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -98,6 +99,19 @@ def curves_3d(bins: np.ndarray, L: int) -> dict:
                                   _ptr(out["area"]), _ptr(out["volume"]))
     if rc != 0:
         raise ValueError(f"oracle_curves_3d failed ({rc})")
+    return out
+
+
+def curves_3d_zrange(bins: np.ndarray, L: int, zlo: int, zhi: int) -> dict:
+    """Curves of only the cells whose doubled z coordinate is in [zlo, zhi]
+    (the whole field is [0, 2d]); disjoint ranges add up."""
+    bins = np.ascontiguousarray(bins, dtype=np.int32)
+    d, h, w = bins.shape
+    out = {k: np.zeros(L, dtype=np.int64) for k in ("ec", "perimeter", "area", "volume")}
+    rc = _load().oracle_curves_3d_zrange(_ptr(bins), d, h, w, L, zlo, zhi, _ptr(out["ec"]), _ptr(out["perimeter"]),
+                                         _ptr(out["area"]), _ptr(out["volume"]))
+    if rc != 0:
+        raise ValueError(f"oracle_curves_3d_zrange failed ({rc})")
     return out
 
 

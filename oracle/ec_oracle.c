@@ -228,11 +228,18 @@ int oracle_curves_2d(const int32_t *bins, int64_t h, int64_t w, int32_t L,
 
 /* ------------------------------------------------------------------- 3D */
 
-/* bins: d*h*w, index (z*h + y)*w + x.  Any output pointer may be NULL. */
-int oracle_curves_3d(const int32_t *bins, int64_t d, int64_t h, int64_t w, int32_t L,
-                     int64_t *ec, int64_t *perim, int64_t *area, int64_t *vol)
+/* bins: d*h*w, index (z*h + y)*w + x.  Any output pointer may be NULL.
+ * Only cells whose doubled z coordinate Z lies in [zlo, zhi] are counted;
+ * the full curves use [0, 2d].  The counts of Eq. EC_formula (and of every
+ * boundary measure) are sums over cells, so curves of disjoint Z ranges add
+ * up to the curves of their union. */
+int oracle_curves_3d_zrange(const int32_t *bins, int64_t d, int64_t h, int64_t w, int32_t L,
+                            int64_t zlo, int64_t zhi,
+                            int64_t *ec, int64_t *perim, int64_t *area, int64_t *vol)
 {
     if (d < 1 || h < 1 || w < 1 || L < 1) return -1;
+    if (zlo < 0) zlo = 0;
+    if (zhi > 2 * d) zhi = 2 * d;
     const int64_t W2 = 2 * w, H2 = 2 * h, D2 = 2 * d, NB = (int64_t)L + 1;
     int nthr = 1;
 #ifdef _OPENMP
@@ -252,7 +259,7 @@ int oracle_curves_3d(const int32_t *bins, int64_t d, int64_t h, int64_t w, int32
         int64_t *cnt = acc + tid * per_thread;
         int64_t *per_d = cnt + 4 * NB, *area_d = cnt + 5 * NB, *vol_d = cnt + 6 * NB;
         #pragma omp for schedule(dynamic, 1)
-        for (int64_t Z = 0; Z <= D2; Z++) {
+        for (int64_t Z = zlo; Z <= zhi; Z++) {
             int64_t sz[2]; int nz = axis_slots(Z, d, sz);
             for (int64_t Y = 0; Y <= H2; Y++) {
                 int64_t sy[2]; int ny = axis_slots(Y, h, sy);
@@ -311,6 +318,12 @@ int oracle_curves_3d(const int32_t *bins, int64_t d, int64_t h, int64_t w, int32
     }
     free(acc);
     return 0;
+}
+
+int oracle_curves_3d(const int32_t *bins, int64_t d, int64_t h, int64_t w, int32_t L,
+                     int64_t *ec, int64_t *perim, int64_t *area, int64_t *vol)
+{
+    return oracle_curves_3d_zrange(bins, d, h, w, L, 0, 2 * d, ec, perim, area, vol);
 }
 
 /* ------------------------------------------- hash-box field (workload input)
