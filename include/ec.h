@@ -94,8 +94,15 @@ int ec_ctx_destroy(ec_ctx *ctx);
  *  EC_OPT_TILE_Z: z planes per work item of the 3D kernels (0 = planner).
  *  EC_OPT_GRID: blocks per launch (0 = planner).
  *  EC_OPT_PROFILE: 1 = bracket the main histogram kernel of every request
- *    with CUDA events on the request's stream (see ec_ctx_profile_read).   */
-enum { EC_OPT_ALGO = 1, EC_OPT_VALIDATE = 2, EC_OPT_TILE_Z = 3, EC_OPT_GRID = 4, EC_OPT_PROFILE = 5 };
+ *    with CUDA events on the request's stream (see ec_ctx_profile_read).
+ *  EC_OPT_HIST_SCHEDULE: how the fast 3D kernel updates its shared-memory
+ *    histogram: 0 = auto, 1 = one atomic per voxel and descriptor,
+ *    2 = warp-aggregated (lanes of a warp with the same level are summed
+ *    first and one lane per level issues the atomics), 3 = two descriptors
+ *    per 32-bit word in two lane-parity copies (half the atomics, fewer
+ *    same-address collisions).  All give identical curves.                 */
+enum { EC_OPT_ALGO = 1, EC_OPT_VALIDATE = 2, EC_OPT_TILE_Z = 3, EC_OPT_GRID = 4, EC_OPT_PROFILE = 5,
+       EC_OPT_HIST_SCHEDULE = 6 };
 int ec_ctx_set_option(ec_ctx *ctx, int option, int64_t value);
 
 /* Summed device time (ms) and count of the main histogram kernel launches

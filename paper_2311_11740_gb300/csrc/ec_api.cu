@@ -133,6 +133,7 @@ int run_curve(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int
     }
     CurvePlan plan;
     plan.algo = ctx->algo;
+    plan.hist_schedule = ctx->hist_schedule;
     plan.tile_z = ctx->tile_z;
     plan.grid = ctx->grid;
     plan.num_sms = ctx->num_sms;
@@ -167,7 +168,7 @@ int ec::enqueue_curve(const CurvePlan &plan, int ndim, const void *field, const 
     EC_CUDA(cudaMemsetAsync(scratch, 0, curve_scratch_bytes(descriptors, L), s));
     const int algo = plan.algo == ALGO_VERTEX ? ALGO_VERTEX : ALGO_VOXEL;
     BinArgs ba{L, dtype, thr};
-    HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0};
+    HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0, plan.hist_schedule};
     int rc;
     if (plan.prof && (rc = prof_begin(plan.prof, s))) return rc;
     if (ndim == 3) {
@@ -282,6 +283,10 @@ int ec_ctx_set_option(ec_ctx *ctx, int option, int64_t value)
     case EC_OPT_GRID:
         if (value < 0 || value > (1 << 20)) { set_error("bad grid"); return EC_ERR_ARG; }
         ctx->grid = (int)value;
+        return EC_OK;
+    case EC_OPT_HIST_SCHEDULE:
+        if (value < 0 || value > 3) { set_error("bad histogram schedule"); return EC_ERR_ARG; }
+        ctx->hist_schedule = (int)value;
         return EC_OK;
     case EC_OPT_PROFILE: {
         std::lock_guard<std::mutex> lock(ctx->mu);

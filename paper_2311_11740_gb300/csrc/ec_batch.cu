@@ -155,6 +155,7 @@ __device__ void item_3d(const BField &F, const BItem &it, const Shared &S, const
     c.p.nd = F.nd;
     c.p.smem_hist = F.smem_hist;
     c.p.err = err;
+    c.p.agg = 0;
     c.fring = nullptr;
     c.kring = S.kring;
     c.bars = nullptr;

@@ -68,7 +68,7 @@ __global__ void k_uniform_check(const float *t, int L, int *uni)
 #define EC_FAST_MIN_BLOCKS 3
 #endif
 
-template <typename T, bool TMA, bool PER, int DM>
+template <typename T, bool TMA, bool PER, int DM, int SCHED = 0>
 __global__ void __launch_bounds__(kThreads, EC_FAST_MIN_BLOCKS)
 k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
 {
@@ -91,6 +91,14 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
         c.sh_hist = (int *)tail;
         for (int i = threadIdx.x; i < p.nd * L; i += kThreads) c.sh_hist[i] = 0;
         tail += ((size_t)p.nd * L * 4 + 15) & ~(size_t)15;
+        c.pw1 = c.pw2 = nullptr;
+        c.pstride = ((L + 31) & ~31) + 1;
+        if (p.pairs) {
+            c.pw1 = (uint32_t *)tail;
+            c.pw2 = c.pw1 + 2 * c.pstride;
+            for (int i = threadIdx.x; i < 4 * c.pstride; i += kThreads) c.pw1[i] = 0u;
+            tail += ((size_t)4 * c.pstride * 4 + 15) & ~(size_t)15;
+        }
         if (p.packed) {
             c.h64 = (unsigned long long *)tail;
             for (int i = threadIdx.x; i < L; i += kThreads) c.h64[i] = 0ull;
@@ -191,14 +199,28 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
         }
         const int nsteps = c.z1 - c.z0 + 3;
         for (int t = 0; t < nsteps; t += 3) {
-            if (!zstep<T, TMA, PER, 0, DM>(c, &tmap, win, t)) return;
-            if (t + 1 < nsteps && !zstep<T, TMA, PER, 1, DM>(c, &tmap, win, t + 1)) return;
-            if (t + 2 < nsteps && !zstep<T, TMA, PER, 2, DM>(c, &tmap, win, t + 2)) return;
+            if (!zstep<T, TMA, PER, 0, DM, SCHED>(c, &tmap, win, t)) return;
+            if (t + 1 < nsteps && !zstep<T, TMA, PER, 1, DM, SCHED>(c, &tmap, win, t + 1)) return;
+            if (t + 2 < nsteps && !zstep<T, TMA, PER, 2, DM, SCHED>(c, &tmap, win, t + 2)) return;
         }
         if (TMA) seq += (uint32_t)(c.z1 - c.z0 + 2);
         if (c.h64) {
             __syncthreads();
             flush_packed<T, PER>(c);
+        }
+    }
+    if (c.sh_hist && p.pairs) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < L; k += kThreads) {
+            int lo, hi;
+            for (int cpy = 0; cpy < 2; cpy++) {
+                pair_decode(c.pw1[cpy * c.pstride + k], lo, hi);
+                if (p.rows[0] >= 0) c.sh_hist[p.rows[0] * L + k] += lo;
+                if (p.rows[3] >= 0) c.sh_hist[p.rows[3] * L + k] += hi;
+                pair_decode(c.pw2[cpy * c.pstride + k], lo, hi);
+                if (p.rows[2] >= 0) c.sh_hist[p.rows[2] * L + k] += lo;
+                if (p.rows[1] >= 0) c.sh_hist[p.rows[1] * L + k] += hi;
+            }
         }
     }
     if (c.sh_hist) {
@@ -231,22 +253,23 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 }
 
 static size_t smem_bytes(bool tma, int dtype_size, int nd, int L, bool smem_hist, bool has_thr, bool packed,
-                         bool per)
+                         bool per, bool pairs)
 {
     size_t b = tma ? (size_t)NS * FSTRIDE * 4 : 0;
     b += (size_t)NK * KWORDS * 4 + NS * 8 + 16;
     if (smem_hist) b += ((size_t)nd * L * 4 + 15) & ~(size_t)15;
     if (smem_hist && packed) b += (size_t)L * 8 + (per ? (((size_t)L * 4 + 15) & ~(size_t)15) : 0);
+    if (smem_hist && pairs) b += ((size_t)4 * (((L + 31) & ~31) + 1) * 4 + 15) & ~(size_t)15;
     if (dtype_size == 1) b += 512;
     else if (has_thr && L <= kThrSmem) b += ((size_t)L * dtype_size + 15) & ~(size_t)15;
     return b;
 }
 
-template <typename T, bool TMA, bool PER, int DM = 0>
+template <typename T, bool TMA, bool PER, int DM = 0, int SCHED = 0>
 static int launch_t(const CUtensorMap &map, const Params &p, size_t smem, int num_sms, int items, int grid_override,
                     cudaStream_t s)
 {
-    auto kern = k_voxel3d_fast<T, TMA, PER, DM>;
+    auto kern = k_voxel3d_fast<T, TMA, PER, DM, SCHED>;
     EC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
@@ -292,6 +315,8 @@ int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, 
     // one packed atomic per voxel needs per-item counts below 2^21 per field:
     // items of at most 64 x 16 x 64 voxels, |change| <= 26 after the offsets
     p.packed = 0;   // 64-bit shared atomics are not native: one 32-bit atomic per descriptor instead
+    p.agg = ha.schedule == 2 ? 1 : 0;
+    p.pairs = 0;
     p.uni = nullptr;
     if (ba.dtype == EC_F32) {
         p.uni = err_flag + 2;
@@ -320,16 +345,25 @@ int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, 
             tma = r == CUDA_SUCCESS;
         }
     }
-    const size_t smem = smem_bytes(tma, dsz, p.nd, p.L, p.smem_hist != 0, ba.thr != nullptr, p.packed != 0, per);
+    if (ha.schedule == 3 && ha.smem_hist && tma && (desc == 13u || desc == 15u)) p.pairs = 1;
+    const size_t smem = smem_bytes(tma, dsz, p.nd, p.L, p.smem_hist != 0, ba.thr != nullptr, p.packed != 0, per,
+                                   p.pairs != 0);
     const int items = (int)items64;
     switch (ba.dtype) {
     case EC_F32:
-        if (tma && p.smem_hist) {
+        if (tma && p.smem_hist && !p.agg) {
             // descriptor sets with compile-time histogram rows
+            if (p.pairs) {
+                if (desc == 13u) return launch_t<float, true, false, 13, 3>(map, p, smem, num_sms, items, grid_override, s);
+                if (desc == 15u) return launch_t<float, true, true, 15, 3>(map, p, smem, num_sms, items, grid_override, s);
+            }
             if (desc == 1u) return launch_t<float, true, false, 1>(map, p, smem, num_sms, items, grid_override, s);
             if (desc == 13u) return launch_t<float, true, false, 13>(map, p, smem, num_sms, items, grid_override, s);
             if (desc == 15u) return launch_t<float, true, true, 15>(map, p, smem, num_sms, items, grid_override, s);
         }
+        if (tma && p.agg)
+            return per ? launch_t<float, true, true, 0, 2>(map, p, smem, num_sms, items, grid_override, s)
+                       : launch_t<float, true, false, 0, 2>(map, p, smem, num_sms, items, grid_override, s);
         if (tma) return per ? launch_t<float, true, true>(map, p, smem, num_sms, items, grid_override, s)
                             : launch_t<float, true, false>(map, p, smem, num_sms, items, grid_override, s);
         return per ? launch_t<float, false, true>(map, p, smem, num_sms, items, grid_override, s)

@@ -39,6 +39,8 @@ struct Params {
     int *err;              // bit 2: a bounded wait gave up
     const int *uni;        // [0] = 1 if the uniform-spacing guess is exact, [1] = its scale (float bits)
     int packed;            // 1: one 64-bit shared atomic per voxel, flushed per work item
+    int agg;               // 1: warp-aggregated shared-memory updates (lanes grouped by level)
+    int pairs;             // 1: two descriptors per 32-bit word, two lane-parity copies (see PairHist)
 };
 
 // ------------------------------------------------------------- mbarriers
@@ -177,6 +179,8 @@ struct Ctx {
     int *sh_hist;
     unsigned long long *h64;   // packed first-level histogram (EC+13 | area+6 << 21 | count << 42)
     unsigned int *h32;         // packed perimeter (perimeter + 12)
+    uint32_t *pw1, *pw2;       // paired first-level words: [EC | count] and [area | perimeter], 2 copies each
+    int pstride;               // words between the two copies (odd multiple of banks apart)
     FBin fb;
     IBin<T> ib;
     int tr, tc;
@@ -222,6 +226,30 @@ __device__ __forceinline__ void flush_packed(Ctx<T> &c)
 // One step of the z walk: bin plane t+z0-1 (if needed), load key plane
 // s+1 into window slot (R+1)%3, and add the contributions of plane s.
 // R = t mod 3 where s = z0 - 3 + t.  Returns false if the block must stop.
+// Paired 16-bit fields in one 32-bit word: value = lo + 65536 * hi with lo a
+// signed 16-bit field (its borrow runs into hi), so any sequence of adds
+// decodes exactly while |lo| and |hi| stay below 2^15.  A thread that sees a
+// field pass 16000 after its add moves the word into the int32 histogram
+// (atomicExch), which keeps both fields far from their limits.
+__device__ __forceinline__ void pair_decode(uint32_t w, int &lo, int &hi)
+{
+    lo = (int)(int16_t)(w & 0xFFFFu);
+    hi = (int)(w - (uint32_t)lo) >> 16;
+}
+
+__device__ __forceinline__ void pair_add(uint32_t *word, uint32_t add, int *row_lo, int *row_hi, uint32_t k)
+{
+    const uint32_t old = atomicAdd(word, add);
+    int lo, hi;
+    pair_decode(old + add, lo, hi);
+    if (lo > 16000 || lo < -16000 || hi > 16000 || hi < -16000) {
+        const uint32_t w = atomicExch(word, 0u);
+        pair_decode(w, lo, hi);
+        if (row_lo) atomicAdd(&row_lo[k], lo);
+        if (row_hi) atomicAdd(&row_hi[k], hi);
+    }
+}
+
 template <int DM, int D>
 constexpr int dm_row() { return ((DM & 1) && D > 0) + ((DM & 2) && D > 1) + ((DM & 4) && D > 2); }
 
@@ -244,7 +272,7 @@ __device__ __forceinline__ void bin_plane_f32(uint32_t *kp, const float *fp, con
     }
 }
 
-template <typename T, bool TMA, bool PER, int R, int DM>
+template <typename T, bool TMA, bool PER, int R, int DM, int SCHED = 0>
 __device__ __forceinline__ bool zstep(Ctx<T> &c, const CUtensorMap *tmap, uint32_t (&win)[3][3][5], int t)
 {
     const int s = c.z0 - 3 + t;
@@ -338,6 +366,29 @@ __device__ __forceinline__ bool zstep(Ctx<T> &c, const CUtensorMap *tmap, uint32
         if constexpr (DM != 0) {
             // descriptor rows fixed at compile time; shared histogram guaranteed
             int *const h = c.sh_hist;
+            if constexpr (SCHED == 3) {
+                const uint32_t cp = (threadIdx.x & 1u) * (uint32_t)c.pstride;
+                int *const r_ec = (DM & 1) ? h + dm_row<DM, 0>() * L : nullptr;
+                int *const r_pe = (DM & 2) ? h + dm_row<DM, 1>() * L : nullptr;
+                int *const r_ar = (DM & 4) ? h + dm_row<DM, 2>() * L : nullptr;
+                int *const r_vo = (DM & 8) ? h + dm_row<DM, 3>() * L : nullptr;
+#pragma unroll
+                for (int v = 0; v < 4; v++) {
+                    const uint32_t k = key[v];
+                    if (k < (uint32_t)L) {
+                        if (DM & 9) {
+                            const uint32_t add = ((DM & 1) ? (uint32_t)ecv[v] : 0u) + ((DM & 8) ? 65536u : 0u);
+                            pair_add(c.pw1 + cp + k, add, r_ec, r_vo, k);
+                        }
+                        if (DM & 6) {
+                            const uint32_t add = ((DM & 4) ? (uint32_t)arv[v] : 0u) +
+                                                 ((DM & 2) ? (uint32_t)pev[v] * 65536u : 0u);
+                            pair_add(c.pw2 + cp + k, add, r_ar, r_pe, k);
+                        }
+                    }
+                }
+                return true;
+            } else {
 #pragma unroll
             for (int v = 0; v < 4; v++) {
                 const uint32_t k = key[v];
@@ -346,6 +397,33 @@ __device__ __forceinline__ bool zstep(Ctx<T> &c, const CUtensorMap *tmap, uint32
                     if (DM & 2) atomicAdd(&h[dm_row<DM, 1>() * L + k], pev[v]);
                     if (DM & 4) atomicAdd(&h[dm_row<DM, 2>() * L + k], arv[v]);
                     if (DM & 8) atomicAdd(&h[dm_row<DM, 3>() * L + k], 1);
+                }
+            }
+            return true;
+            }
+        }
+        if constexpr (SCHED == 2) {
+            // warp-aggregated update with descriptor rows known at run time
+            const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const uint32_t k = key[v] < (uint32_t)L ? key[v] : 0xFFFFFFFFu;
+                const uint32_t grp = __match_any_sync(0xFFFFFFFFu, k);
+                const uint32_t pk = (uint32_t)(ecv[v] + 13) | ((uint32_t)(arv[v] + 6) << 10) |
+                                    ((uint32_t)(pev[v] + 12) << 20);
+                const uint32_t sum = __reduce_add_sync(grp, pk);
+                if (k != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(grp) - 1)) {
+                    const int n = __popc(grp);
+                    const int vals[4] = {(int)(sum & 1023u) - 13 * n, (int)((sum >> 20) & 1023u) - 12 * n,
+                                         (int)((sum >> 10) & 1023u) - 6 * n, n};
+#pragma unroll
+                    for (int dsc = 0; dsc < kMaxDesc; dsc++) {
+                        const int r = c.p.rows[dsc];
+                        if (r < 0) continue;
+                        if (c.sh_hist) atomicAdd(&c.sh_hist[r * L + k], vals[dsc]);
+                        else atomicAdd((unsigned long long *)&c.p.hist[(size_t)r * L + k],
+                                       (unsigned long long)(long long)vals[dsc]);
+                    }
                 }
             }
             return true;

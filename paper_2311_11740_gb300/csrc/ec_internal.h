@@ -47,6 +47,7 @@ struct HistArgs {
     RowMap rows;
     long long *hist;    // global int64 [nd][L]
     int smem_hist;      // 1: block-private shared-memory int32 histogram, flushed at the end
+    int schedule = 0;   // shared-memory update schedule: 0 auto, 1 one atomic per voxel, 2 warp-aggregated
 };
 
 // Launch helpers implemented in ec_kernels.cu.  All are stream-ordered and
@@ -105,6 +106,7 @@ struct ec_ctx {
     int tile_z = 0;
     int grid = 0;
     int profile = 0;
+    int hist_schedule = 0;
     void *ws = nullptr;        // device scratch: [flags 256 B][int64 histogram]
     size_t ws_bytes = 0;
     int *host_flag = nullptr;  // pinned, for validation read-back
@@ -118,6 +120,7 @@ namespace ec {
 // How to launch one curve request.
 struct CurvePlan {
     int algo = ALGO_AUTO;
+    int hist_schedule = 0;
     int tile_z = 0;
     int grid = 0;
     int num_sms = 1;

@@ -106,7 +106,7 @@ extern "C" int ec_curve_3d_stream(ec_ctx *ctx, const void *host_field, ec_slab_f
     EC_CUDA(cudaStreamSynchronize(res.comp));
 
     const BinArgs ba{L, dtype, thr_dev};
-    const HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0};
+    const HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0, ctx->hist_schedule};
     const int64_t nslabs = (d + S - 1) / S;
     for (int64_t i = 0; i < nslabs; i++) {
         const int b = (int)(i % nbuf);

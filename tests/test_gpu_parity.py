@@ -235,3 +235,17 @@ def test_uniform_threshold_binning_edges(ctx, lo, hi, L):
                            np.nextafter(picks, np.float32(-np.inf)), special]).astype(np.float32)
     f = rng.permutation(np.resize(vals, 24 * 25 * 28)).astype(np.float32).reshape(24, 25, 28)
     check(ctx, f, thr, L, algos=[ec.ALGO_VOXEL])
+
+
+@pytest.mark.parametrize("desc", [1, 5, 13, 15, 8, 2])
+def test_histogram_schedules_agree(ctx, desc):
+    """One atomic per voxel and warp-aggregated updates give the oracle's curves."""
+    f, thr = workloads.config3(n=72, nblobs=30, L=300)
+    f, thr = f.numpy(), thr.numpy()
+    want = oracle.ec_curves(f, thr, 300, 26, desc)
+    try:
+        for sched in (1, 2, 3, 0):
+            ctx.set_option(ec.EC_OPT_HIST_SCHEDULE, sched)
+            np.testing.assert_array_equal(gpu_curves(ctx, f, thr, 300, 26, desc), want, err_msg=f"schedule {sched}")
+    finally:
+        ctx.set_option(ec.EC_OPT_HIST_SCHEDULE, 0)
