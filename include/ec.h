@@ -100,10 +100,20 @@ int ec_ctx_destroy(ec_ctx *ctx);
  *    2 = warp-aggregated (lanes of a warp with the same level are summed
  *    first and one lane per level issues the atomics), 3 = two descriptors
  *    per 32-bit word in two lane-parity copies (half the atomics, fewer
- *    same-address collisions).  All give identical curves.                 */
+ *    same-address collisions).  All give identical curves.
+ *  EC_OPT_AUTOTUNE: 1 = the first request of every shape class (ndim, dtype,
+ *    level-count and size buckets, descriptors) times the candidate plans
+ *    (tile depth, grid, schedule) on itself, synchronously, and later
+ *    requests of the class use the fastest.  With the environment variable
+ *    EC_AUTOTUNE_CACHE naming a file, tuned plans persist there as JSON.   */
 enum { EC_OPT_ALGO = 1, EC_OPT_VALIDATE = 2, EC_OPT_TILE_Z = 3, EC_OPT_GRID = 4, EC_OPT_PROFILE = 5,
-       EC_OPT_HIST_SCHEDULE = 6 };
+       EC_OPT_HIST_SCHEDULE = 6, EC_OPT_AUTOTUNE = 7 };
 int ec_ctx_set_option(ec_ctx *ctx, int option, int64_t value);
+
+/* The tuned plan of a shape class, if the autotuner has one:
+ * out = {tile_z, grid, schedule}; EC_ERR_ARG when the class is not tuned yet. */
+int ec_tuned_plan(ec_ctx *ctx, int32_t ndim, int dtype, int32_t L, uint32_t descriptors, const int64_t *dims,
+                  int32_t out[3]);
 
 /* Summed device time (ms) and count of the main histogram kernel launches
  * bracketed since the last read (EC_OPT_PROFILE); waits for the last one to

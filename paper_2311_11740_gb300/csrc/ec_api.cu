@@ -138,6 +138,10 @@ int run_curve(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int
     plan.grid = ctx->grid;
     plan.num_sms = ctx->num_sms;
     plan.prof = ctx->profile ? ctx : nullptr;
+    if (ctx->autotune && plan.algo != ALGO_VERTEX) {
+        rc = tuned_plan(ctx, ndim, field, dims, dtype, thr, L, connectivity, descriptors, out, s, plan);
+        if (rc) return rc;
+    }
     rc = enqueue_curve(plan, ndim, field, dims, dtype, thr, L, connectivity, descriptors, out, ctx->ws, s);
     if (rc) return rc;
     if (ctx->validate) {
@@ -261,6 +265,7 @@ int ec_ctx_destroy(ec_ctx *ctx)
         if (ctx->host_flag) cudaFreeHost(ctx->host_flag);
         for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
         batch_release(ctx);
+        tune_release(ctx);
     }
     delete ctx;
     return EC_OK;
@@ -284,6 +289,7 @@ int ec_ctx_set_option(ec_ctx *ctx, int option, int64_t value)
         if (value < 0 || value > (1 << 20)) { set_error("bad grid"); return EC_ERR_ARG; }
         ctx->grid = (int)value;
         return EC_OK;
+    case EC_OPT_AUTOTUNE: ctx->autotune = value ? 1 : 0; return EC_OK;
     case EC_OPT_HIST_SCHEDULE:
         if (value < 0 || value > 3) { set_error("bad histogram schedule"); return EC_ERR_ARG; }
         ctx->hist_schedule = (int)value;

@@ -113,6 +113,8 @@ struct ec_ctx {
     std::vector<cudaEvent_t> prof_events;   // start/stop pairs of the main kernel
     size_t prof_used = 0;
     void *batch_state = nullptr;            // ec_batch tables, graph and pinned staging
+    void *tune_cache = nullptr;             // autotuned plans per shape class
+    int autotune = 0;
     std::mutex mu;
 };
 
@@ -134,6 +136,11 @@ int enqueue_curve(const CurvePlan &plan, int ndim, const void *field, const int6
                   cudaStream_t s);
 // Grow the context's scratch to at least `bytes` (device-synchronising when it grows).
 int ensure_scratch(ec_ctx *ctx, size_t bytes);
+// Autotuner (EC_OPT_AUTOTUNE): fill `plan` from the cache, timing the
+// candidate plans on this request first when its shape class is new.
+int tuned_plan(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int dtype, const void *thr,
+               int32_t L, int connectivity, uint32_t desc, int64_t *out, cudaStream_t s, CurvePlan &plan);
+void tune_release(ec_ctx *ctx);
 // Free what ec_batch keeps in a context.
 void batch_release(ec_ctx *ctx);
 // Kernel timing (EC_OPT_PROFILE): bracket the main histogram kernel of a request.

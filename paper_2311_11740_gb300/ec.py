@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libec.so")
 EC_U8, EC_U16, EC_F32 = 0, 1, 2
 EC_DESC_EC, EC_DESC_PERIMETER, EC_DESC_AREA, EC_DESC_VOLUME = 1, 2, 4, 8
 EC_OPT_ALGO, EC_OPT_VALIDATE, EC_OPT_TILE_Z, EC_OPT_GRID, EC_OPT_PROFILE, EC_OPT_HIST_SCHEDULE = 1, 2, 3, 4, 5, 6
+EC_OPT_AUTOTUNE = 7
 ALGO_AUTO, ALGO_VOXEL, ALGO_VERTEX = 0, 1, 2
 STATUS = {0: "EC_OK", 1: "EC_ERR_ARG", 2: "EC_ERR_DTYPE", 3: "EC_ERR_UNSUPPORTED", 4: "EC_ERR_OOM",
           5: "EC_ERR_CUDA", 6: "EC_ERR_TIMEOUT", 7: "EC_ERR_OVERFLOW", 8: "EC_ERR_BUSY"}
@@ -75,6 +76,7 @@ def lib():
             L.ec_server_wait.argtypes = [P, ctypes.c_uint64, I64, ctypes.POINTER(ctypes.c_int32)]
             L.ec_server_stats.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
             L.ec_server_destroy.argtypes = [P]
+            L.ec_tuned_plan.argtypes = [P, I32, ctypes.c_int, I32, U32, ctypes.POINTER(I64), ctypes.POINTER(I32)]
             L.ec_gen_hashbox_u16.argtypes = [ctypes.c_uint64, I64, I64, I64, I64, I64, I64, P, P]
             _lib = L
     return _lib
@@ -118,6 +120,12 @@ class Context:
 
     def set_option(self, option: int, value: int):
         _check(lib().ec_ctx_set_option(self.handle, option, int(value)))
+
+    def tuned_plan(self, ndim, dtype, L, descriptors, dims):
+        """(tile_z, grid, schedule) the autotuner chose for a shape class, or None."""
+        out = (ctypes.c_int32 * 3)()
+        rc = lib().ec_tuned_plan(self.handle, ndim, dtype, L, descriptors, _dims(dims), out)
+        return None if rc else tuple(out)
 
     def profile_read(self):
         """(summed kernel ms, launches) since the last read (EC_OPT_PROFILE)."""
