@@ -181,7 +181,11 @@ int ec::enqueue_curve(const CurvePlan &plan, int ndim, const void *field, const 
         if (rc == EC_ERR_UNSUPPORTED)
             rc = launch_curve_3d(field, dims, ba, ha, algo, plan.tile_z, plan.grid, plan.num_sms, s);
     } else {
-        rc = launch_curve_2d(field, dims, ba, ha, connectivity, algo, plan.grid, plan.num_sms, s);
+        rc = EC_ERR_UNSUPPORTED;
+        if (algo == ALGO_VOXEL)
+            rc = launch_fast_2d(field, dims, ba, ha, connectivity, plan.grid, plan.num_sms, flags, s);
+        if (rc == EC_ERR_UNSUPPORTED)
+            rc = launch_curve_2d(field, dims, ba, ha, connectivity, algo, plan.grid, plan.num_sms, s);
     }
     if (rc) return rc;
     if (plan.prof && (rc = prof_end(plan.prof, s))) return rc;

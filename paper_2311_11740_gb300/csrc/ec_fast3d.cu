@@ -234,6 +234,17 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
 
 // ------------------------------------------------------------------- host
 
+}  // namespace fast3d
+
+int launch_uniform_check(const float *thr, int32_t L, int *uni, cudaStream_t s)
+{
+    fast3d::k_uniform_check<<<1, 256, 0, s>>>(thr, L, uni);
+    EC_CUDA(cudaGetLastError());
+    return EC_OK;
+}
+
+namespace fast3d {
+
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;

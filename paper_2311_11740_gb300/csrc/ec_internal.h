@@ -63,6 +63,12 @@ int launch_curve_2d(const void *field, const int64_t dims[2], const BinArgs &ba,
 // as never active (slab halos at the field's ends).
 int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha, int tile_z,
                    int grid_override, int num_sms, int *err_flag, cudaStream_t s, const int zrange[4] = nullptr);
+// The fast per-pixel 2D kernel; EC_ERR_UNSUPPORTED without launching when a
+// request does not fit it (more than 32767 levels).
+int launch_fast_2d(const void *field, const int64_t dims[2], const BinArgs &ba, const HistArgs &ha, int connectivity,
+                   int grid_override, int num_sms, int *err_flag, cudaStream_t s);
+// Spacing check of float thresholds for the fast binning (writes uni[0..1]).
+int launch_uniform_check(const float *thr, int32_t L, int *uni, cudaStream_t s);
 // Running sum over levels and exact division by each row's scale.
 int launch_scan(const long long *hist, int nd, int32_t L, const int32_t scale[kMaxDesc],
                 int64_t *out, int *err_flag, cudaStream_t s);
