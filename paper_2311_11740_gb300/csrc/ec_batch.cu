@@ -2,7 +2,7 @@
 //
 // Sec. 4 of the paper notes that small images gain little from parallelising
 // one image at a time.  Here every field of a batch is cut into work items
-// (64 x 16 x 64 voxel tiles for 3D fields, 256 x 64 pixel tiles for 2D
+// (64 x 16 x 64 voxel tiles for 3D fields, 1024 x 64 pixel tiles for 2D
 // fields); one persistent kernel pulls items from a global counter, so
 // fields of any size and mix share the whole GPU.  Per item a block:
 //   1. loads the item's field parameters and binning tables into shared
@@ -24,7 +24,7 @@
 #include <string>
 #include <vector>
 
-#include "ec_fast3d.cuh"
+#include "ec_fast2d.cuh"
 
 namespace ec {
 
@@ -193,60 +193,41 @@ __device__ __forceinline__ uint32_t bin2(T v, const FBin &fb, const IBin<T> &ib)
     else return ib(v);
 }
 
-// One 2D item: 256 columns of rows [z0, z1), per-pixel regrouped changes.
-template <typename T>
+// One 2D item: a 1024-column strip (x0) over rows [z0, z1), with the fast
+// 2D row walk of ec_fast2d.cuh.
+template <typename T, bool CONN4>
 __device__ void item_2d(const BField &F, const BItem &it, const Shared &S, const FBin &fb)
 {
-    const IBin<T> ib = make_ibin<T>(F, S);
-    const int64_t H = F.dims[1], W = F.dims[2];
-    const T *f = (const T *)F.field;
-    const int L = F.L;
-    uint16_t *ring = (uint16_t *)S.kring;   // 4 rows of 258 keys
-    constexpr int RW = 258;
-    const int tx = threadIdx.x;
-    const int64_t x0 = it.x0;
-    auto stage = [&](int64_t y, int slot) {
-        for (int i = tx; i < RW; i += blockDim.x) {
-            const int64_t gx = x0 - 1 + i;
-            uint32_t key = (uint32_t)L;
-            if (y >= 0 && y < H && gx >= 0 && gx < W) key = bin2<T>(f[y * W + gx], fb, ib);
-            ring[slot * RW + i] = (uint16_t)key;
-        }
-    };
-    const int y0 = it.z0, y1 = it.z1;
-    stage(y0 - 1, (y0 + 3) & 3);
-    stage(y0, (y0 + 4) & 3);
-    int *sh = F.smem_hist ? S.sh_hist : nullptr;
-    for (int y = y0; y < y1; y++) {
-        stage(y + 1, (y + 5) & 3);
-        __syncthreads();
-        const uint16_t *r0 = ring + ((y + 3) & 3) * RW, *r1 = ring + ((y + 4) & 3) * RW,
-                       *r2 = ring + ((y + 5) & 3) * RW;
-        const uint32_t kc = r1[tx + 1];
-        if (x0 + tx < W && kc < (uint32_t)L) {
-            uint32_t P = 0;
-            const uint16_t *rr[3] = {r0, r1, r2};
+    fast2d::Ctx2<T> c;
+    c.p = fast2d::Params{};
+    c.p.field = F.field;
+    c.p.H = F.dims[1];
+    c.p.W = F.dims[2];
+    c.p.L = F.L;
+    c.p.thr = F.thr;
+    c.p.hist = F.hist;
+    for (int i = 0; i < kMaxDesc; i++) c.p.rows[i] = F.rows[i];
+    c.p.nd = F.nd;
+    c.p.smem_hist = F.smem_hist;
+    c.p.conn4 = CONN4 ? 1 : 0;
+    c.ring = S.kring;
+    c.sh_hist = F.smem_hist ? S.sh_hist : nullptr;
+    c.fb = fb;
+    c.ib = make_ibin<T>(F, S);
+    c.x0 = it.x0;
+    c.y0 = it.z0;
+    c.y1 = it.z1;
+    c.interior = c.x0 >= 2 && c.x0 + fast2d::SW + 2 <= c.p.W;
+    uint32_t win[3][5];
 #pragma unroll
-            for (int dy = -1; dy <= 1; dy++)
+    for (int a = 0; a < 3; a++)
 #pragma unroll
-                for (int dx = -1; dx <= 1; dx++) {
-                    if (dx == 0 && dy == 0) continue;
-                    const uint32_t kn = rr[dy + 1][tx + 1 + dx];
-                    const bool lower = dy < 0 || (dy == 0 && dx < 0);
-                    P |= (uint32_t)(lower ? (kn <= kc) : (kn < kc)) << ((dx + 1) + 3 * (dy + 1));
-                }
-            const Delta2 d = pixel_delta_2d(P);
-            const int vals[3] = {F.conn4 ? d.ec4 : d.ec8, d.per, 1};
-#pragma unroll
-            for (int q = 0; q < 3; q++) {
-                const int r = F.rows[q];
-                if (r < 0 || vals[q] == 0) continue;
-                if (sh) atomicAdd(&sh[r * L + kc], vals[q]);
-                else atomicAdd((unsigned long long *)&F.hist[(size_t)r * L + kc],
-                               (unsigned long long)(long long)vals[q]);
-            }
-        }
-        __syncthreads();
+        for (int e = 0; e < 5; e++) win[a][e] = 0;
+    const int nsteps = c.y1 - c.y0 + 2;
+    for (int t = 0; t < nsteps; t += 3) {
+        fast2d::ystep<T, CONN4, 0, 0>(c, win, t);
+        if (t + 1 < nsteps) fast2d::ystep<T, CONN4, 1, 0>(c, win, t + 1);
+        if (t + 2 < nsteps) fast2d::ystep<T, CONN4, 2, 0>(c, win, t + 2);
     }
 }
 
@@ -325,10 +306,18 @@ k_batch(const BField *__restrict__ fields, const BItem *__restrict__ items, int 
             default: per ? item_3d<uint8_t, true>(F, it, S, fb, err) : item_3d<uint8_t, false>(F, it, S, fb, err); break;
             }
         } else {
-            switch (F.dtype) {
-            case EC_F32: item_2d<float>(F, it, S, fb); break;
-            case EC_U16: item_2d<uint16_t>(F, it, S, fb); break;
-            default: item_2d<uint8_t>(F, it, S, fb); break;
+            if (F.conn4) {
+                switch (F.dtype) {
+                case EC_F32: item_2d<float, true>(F, it, S, fb); break;
+                case EC_U16: item_2d<uint16_t, true>(F, it, S, fb); break;
+                default: item_2d<uint8_t, true>(F, it, S, fb); break;
+                }
+            } else {
+                switch (F.dtype) {
+                case EC_F32: item_2d<float, false>(F, it, S, fb); break;
+                case EC_U16: item_2d<uint16_t, false>(F, it, S, fb); break;
+                default: item_2d<uint8_t, false>(F, it, S, fb); break;
+                }
             }
         }
         __syncthreads();
@@ -435,7 +424,7 @@ extern "C" int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, voi
         } else {
             F.dims[0] = 1; F.dims[1] = d.dims[0]; F.dims[2] = d.dims[1];
             for (int64_t y = 0; y < d.dims[0]; y += 64)
-                for (int64_t x = 0; x < d.dims[1]; x += 256) {
+                for (int64_t x = 0; x < d.dims[1]; x += fast2d::SW) {
                     items.push_back(BItem{f, (int)x, 0, (int)y, (int)std::min<int64_t>(y + 64, d.dims[0])});
                     cnt++;
                 }
