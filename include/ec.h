@@ -166,7 +166,10 @@ int ec_curve_3d_noalloc(const void *field_dev, const int64_t dims[3], int dtype,
  * ignored) into dst_dev (C-contiguous (z1-z0) x h x w of dtype) and return 0.
  * thresholds_host: L values on the host (or NULL = identity).  out_host:
  * int64 [popcount(descriptors)][L] on the host, written before return (the
- * call is synchronous).  Results are bit-identical to ec_curve_3d. */
+ * call is synchronous).  Results are bit-identical to ec_curve_3d.  The slab
+ * buffers, their two streams and events stay in the context for the next
+ * call (reallocated when a call needs more memory, or when they exceed that
+ * call's cap) and are freed by ec_ctx_destroy. */
 typedef int (*ec_slab_fn)(void *user, int64_t z0, int64_t z1, void *dst_dev, void *stream);
 int ec_curve_3d_stream(ec_ctx *ctx, const void *host_field, ec_slab_fn producer, void *user,
                        const int64_t dims[3], int dtype, const void *thresholds_host,

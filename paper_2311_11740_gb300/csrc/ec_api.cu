@@ -270,6 +270,7 @@ int ec_ctx_destroy(ec_ctx *ctx)
         for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
         batch_release(ctx);
         tune_release(ctx);
+        stream_release(ctx);
     }
     delete ctx;
     return EC_OK;

@@ -120,6 +120,7 @@ struct ec_ctx {
     size_t prof_used = 0;
     void *batch_state = nullptr;            // ec_batch tables, graph and pinned staging
     void *tune_cache = nullptr;             // autotuned plans per shape class
+    void *stream_state = nullptr;           // streaming buffers, streams and events
     int autotune = 0;
     std::mutex mu;
 };
@@ -149,6 +150,7 @@ int tuned_plan(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, in
 void tune_release(ec_ctx *ctx);
 // Free what ec_batch keeps in a context.
 void batch_release(ec_ctx *ctx);
+void stream_release(ec_ctx *ctx);
 // Kernel timing (EC_OPT_PROFILE): bracket the main histogram kernel of a request.
 int prof_begin(ec_ctx *ctx, cudaStream_t s);
 int prof_end(ec_ctx *ctx, cudaStream_t s);

@@ -28,8 +28,12 @@ namespace {
 
 int dtype_size(int dtype) { return dtype == EC_F32 ? 4 : (dtype == EC_U16 ? 2 : 1); }
 
+// Streams, events and device memory of the streaming path, kept in the
+// context between calls (the memory is reallocated when a call needs more, or
+// when it would not fit the call's cap).
 struct StreamRes {
     void *mem = nullptr;
+    size_t bytes = 0;
     cudaStream_t comp = nullptr, side = nullptr;
     cudaEvent_t filled[3] = {nullptr, nullptr, nullptr}, freed[3] = {nullptr, nullptr, nullptr};
     ~StreamRes()
@@ -46,7 +50,25 @@ struct StreamRes {
     }
 };
 
+int stream_setup(StreamRes &res)
+{
+    if (res.comp) return EC_OK;
+    EC_CUDA(cudaStreamCreateWithFlags(&res.comp, cudaStreamNonBlocking));
+    EC_CUDA(cudaStreamCreateWithFlags(&res.side, cudaStreamNonBlocking));
+    for (int i = 0; i < 3; i++) {
+        EC_CUDA(cudaEventCreateWithFlags(&res.filled[i], cudaEventDisableTiming));
+        EC_CUDA(cudaEventCreateWithFlags(&res.freed[i], cudaEventDisableTiming));
+    }
+    return EC_OK;
+}
+
 }  // namespace
+
+void ec::stream_release(ec_ctx *ctx)
+{
+    delete (StreamRes *)ctx->stream_state;
+    ctx->stream_state = nullptr;
+}
 
 extern "C" int ec_curve_3d_stream(ec_ctx *ctx, const void *host_field, ec_slab_fn producer, void *user,
                                   const int64_t dims[3], int dtype, const void *thresholds_host, int32_t L,
@@ -81,12 +103,26 @@ extern "C" int ec_curve_3d_stream(ec_ctx *ctx, const void *host_field, ec_slab_f
     const size_t buf_bytes = (size_t)(S + 2) * plane;
     const size_t total = fixed + (size_t)nbuf * buf_bytes;
 
-    StreamRes res;
-    cudaError_t e = cudaMalloc(&res.mem, total);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        set_error("cannot allocate %zu bytes for streaming", total);
-        return EC_ERR_OOM;
+    if (!ctx->stream_state) ctx->stream_state = new StreamRes();
+    StreamRes &res = *(StreamRes *)ctx->stream_state;
+    rc = stream_setup(res);
+    if (rc) return rc;
+    if (res.mem && (res.bytes < total || (device_mem_cap > 0 && res.bytes > device_mem_cap))) {
+        EC_CUDA(cudaStreamSynchronize(res.comp));
+        EC_CUDA(cudaStreamSynchronize(res.side));
+        cudaFree(res.mem);
+        res.mem = nullptr;
+        res.bytes = 0;
+    }
+    if (!res.mem) {
+        cudaError_t e = cudaMalloc(&res.mem, total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            res.mem = nullptr;
+            set_error("cannot allocate %zu bytes for streaming", total);
+            return EC_ERR_OOM;
+        }
+        res.bytes = total;
     }
     char *base = (char *)res.mem;
     int *flags = (int *)base;
@@ -94,12 +130,6 @@ extern "C" int ec_curve_3d_stream(ec_ctx *ctx, const void *host_field, ec_slab_f
     long long *hist = (long long *)(base + 256 + ((size_t)L * dsz + 255) / 256 * 256);
     int64_t *out_dev = (int64_t *)(hist + (size_t)rows.nd * L);
     char *bufs = base + fixed;
-    EC_CUDA(cudaStreamCreateWithFlags(&res.comp, cudaStreamNonBlocking));
-    EC_CUDA(cudaStreamCreateWithFlags(&res.side, cudaStreamNonBlocking));
-    for (int i = 0; i < nbuf; i++) {
-        EC_CUDA(cudaEventCreateWithFlags(&res.filled[i], cudaEventDisableTiming));
-        EC_CUDA(cudaEventCreateWithFlags(&res.freed[i], cudaEventDisableTiming));
-    }
     EC_CUDA(cudaMemsetAsync(base, 0, fixed, res.comp));
     if (thresholds_host)
         EC_CUDA(cudaMemcpyAsync(thr_dev, thresholds_host, (size_t)L * dsz, cudaMemcpyHostToDevice, res.comp));
