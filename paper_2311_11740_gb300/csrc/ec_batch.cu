@@ -77,22 +77,12 @@ __device__ int load_binning(const BField &F, const Shared &S, FBin &fb)
         fb.L = L;
         fb.t0 = gt[0];
         fb.tl = gt[L - 1];
-        fb.inv = (L > 1 && fb.tl > fb.t0) ? (float)(L - 1) / (fb.tl - fb.t0) : 0.f;
-        // same interval-end test as k_uniform_check
-        int ok = (fb.t0 == fb.t0 && fb.tl == fb.tl) ? 1 : 0;
-        for (int k = 1 + threadIdx.x; k <= L; k += blockDim.x) {
-            const float lo = gt[k - 1];
-            if (lo != lo) { ok = 0; continue; }
-            if (k == L) {
-                if (lo < INFINITY && bin_guess(nextafterf(lo, INFINITY), fb.t0, fb.inv, L) < L - 1) ok = 0;
-                continue;
-            }
-            const float hi = gt[k];
-            if (hi != hi) { ok = 0; continue; }
-            if (!(lo < hi)) continue;
-            if (bin_guess(nextafterf(lo, INFINITY), fb.t0, fb.inv, L) < k - 1) ok = 0;
-            if (bin_guess(hi, fb.t0, fb.inv, L) > k) ok = 0;
-        }
+        guess_params(fb.t0, fb.tl, L, fb.inv, fb.off);
+        fb.lm1 = (float)(L - 1);
+        // same per-level test as k_uniform_check
+        int ok = 1;
+        for (int k = threadIdx.x; k <= L; k += blockDim.x)
+            if (!guess_ok_for_level(gt, L, k, fb.inv, fb.off)) ok = 0;
         fb.uniform = __syncthreads_and(ok);
         return fb.uniform;
     }
@@ -161,12 +151,11 @@ __device__ void item_3d(const BField &F, const BItem &it, const Shared &S, const
     c.bars = nullptr;
     c.abort_flag = S.abort_flag;
     c.sh_hist = F.smem_hist ? S.sh_hist : nullptr;
-    c.h64 = nullptr;
-    c.h32 = nullptr;
     c.fb = fb;
     c.ib = make_ibin<T>(F, S);
     c.tr = threadIdx.x >> 4;
     c.tc = threadIdx.x & 15;
+    c.bin3 = ~0u;
     c.x0 = it.x0; c.y0 = it.y0; c.z0 = it.z0; c.z1 = it.z1;
     c.interior = c.x0 >= 4 && c.x0 + TXF + 4 <= c.p.W;
     c.base = 0;

@@ -56,10 +56,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_pixel2d_fast(Params p)
         c.fb.t0 = gt[0];
         c.fb.tl = gt[L - 1];
         c.fb.inv = (L > 1 && c.fb.tl > c.fb.t0) ? (float)(L - 1) / (c.fb.tl - c.fb.t0) : 0.f;
+        c.fb.lm1 = (float)(L - 1);
+        c.fb.off = 0.f;
         c.fb.uniform = 0;
         if (p.uni && p.uni[0]) {
             c.fb.uniform = 1;
             c.fb.inv = __int_as_float(p.uni[1]);
+            c.fb.off = __int_as_float(p.uni[2]);
         }
     } else if constexpr (sizeof(T) == 2) {
         const uint16_t *gt = (const uint16_t *)p.thr;

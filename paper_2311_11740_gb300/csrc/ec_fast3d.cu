@@ -34,33 +34,22 @@ namespace ec {
 namespace fast3d {
 
 // Decide whether bin_guess is always the true bin or one below it, for every
-// float: the guess is monotone in x, so it suffices to check both ends of
-// every level's interval (t_{k-1}, t_k] and the interval above t_{L-1}.
-// Writes uni[0] (1 = fast path exact) and uni[1] (the scale, float bits).
+// float (guess_ok_for_level on every level 0..L).  Writes uni[0] (1 = fast
+// path exact) and uni[1], uni[2] (the guess's scale and offset, float bits).
 __global__ void k_uniform_check(const float *t, int L, int *uni)
 {
     __shared__ int ok;
-    const float t0 = t[0], tl = t[L - 1];
-    const float inv = (L > 1 && tl > t0) ? (float)(L - 1) / (tl - t0) : 0.f;
-    if (threadIdx.x == 0) ok = (t0 == t0 && tl == tl) ? 1 : 0;
+    float inv, off;
+    guess_params(t[0], t[L - 1], L, inv, off);
+    if (threadIdx.x == 0) ok = 1;
     __syncthreads();
-    for (int k = 1 + threadIdx.x; k <= L; k += blockDim.x) {
-        const float lo = t[k - 1];
-        if (lo != lo) { ok = 0; continue; }
-        if (k == L) {
-            if (lo < INFINITY && bin_guess(nextafterf(lo, INFINITY), t0, inv, L) < L - 1) ok = 0;
-            continue;
-        }
-        const float hi = t[k];
-        if (hi != hi) { ok = 0; continue; }
-        if (!(lo < hi)) continue;   // empty interval
-        if (bin_guess(nextafterf(lo, INFINITY), t0, inv, L) < k - 1) ok = 0;
-        if (bin_guess(hi, t0, inv, L) > k) ok = 0;
-    }
+    for (int k = threadIdx.x; k <= L; k += blockDim.x)
+        if (!guess_ok_for_level(t, L, k, inv, off)) ok = 0;
     __syncthreads();
     if (threadIdx.x == 0) {
         uni[0] = ok;
         uni[1] = __float_as_int(inv);
+        uni[2] = __float_as_int(off);
     }
 }
 
@@ -74,7 +63,7 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     // layout: [float ring NS*FSTRIDE*4 (TMA only)] [key ring NK*KWORDS*4] [mbar NS*8] [abort 16]
-    //         [hist nd*L*4] [thresholds / byte table]
+    //         [hist nd*(L+1)*4] [thresholds / byte table]
     Ctx<T> c;
     c.p = p;
     const size_t fbytes = TMA ? (size_t)NS * FSTRIDE * sizeof(float) : 0;
@@ -85,12 +74,10 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
     unsigned char *tail = (unsigned char *)(c.bars + NS) + 16;
     const int L = p.L;
     c.sh_hist = nullptr;
-    c.h64 = nullptr;
-    c.h32 = nullptr;
     if (p.smem_hist) {
         c.sh_hist = (int *)tail;
-        for (int i = threadIdx.x; i < p.nd * L; i += kThreads) c.sh_hist[i] = 0;
-        tail += ((size_t)p.nd * L * 4 + 15) & ~(size_t)15;
+        for (int i = threadIdx.x; i < p.nd * (L + 1); i += kThreads) c.sh_hist[i] = 0;
+        tail += ((size_t)p.nd * (L + 1) * 4 + 15) & ~(size_t)15;
         c.pw1 = c.pw2 = nullptr;
         c.pstride = ((L + 31) & ~31) + 1;
         if (p.pairs) {
@@ -98,16 +85,6 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
             c.pw2 = c.pw1 + 2 * c.pstride;
             for (int i = threadIdx.x; i < 4 * c.pstride; i += kThreads) c.pw1[i] = 0u;
             tail += ((size_t)4 * c.pstride * 4 + 15) & ~(size_t)15;
-        }
-        if (p.packed) {
-            c.h64 = (unsigned long long *)tail;
-            for (int i = threadIdx.x; i < L; i += kThreads) c.h64[i] = 0ull;
-            tail += (size_t)L * 8;
-            if (PER) {
-                c.h32 = (unsigned int *)tail;
-                for (int i = threadIdx.x; i < L; i += kThreads) c.h32[i] = 0u;
-                tail += ((size_t)L * 4 + 15) & ~(size_t)15;
-            }
         }
     }
     c.fb = FBin{};
@@ -125,10 +102,13 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
         c.fb.t0 = gt[0];
         c.fb.tl = gt[L - 1];
         c.fb.inv = (L > 1 && c.fb.tl > c.fb.t0) ? (float)(L - 1) / (c.fb.tl - c.fb.t0) : 0.f;
+        c.fb.lm1 = (float)(L - 1);
+        c.fb.off = 0.f;
         c.fb.uniform = 0;
         if (p.uni && p.uni[0]) {
             c.fb.uniform = 1;
             c.fb.inv = __int_as_float(p.uni[1]);
+            c.fb.off = __int_as_float(p.uni[2]);
         }
     } else if constexpr (sizeof(T) == 2) {
         const uint16_t *gt = (const uint16_t *)p.thr;
@@ -168,6 +148,7 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
 
     c.tr = threadIdx.x >> 4;
     c.tc = threadIdx.x & 15;
+    c.bin3 = bin3_offsets(threadIdx.x);
     c.parity = 0;
     uint32_t seq = 0;
     const int nitems = p.nbx * p.nby * p.nbz;
@@ -204,10 +185,6 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
             if (t + 2 < nsteps && !zstep<T, TMA, PER, 2, DM, SCHED>(c, &tmap, win, t + 2)) return;
         }
         if (TMA) seq += (uint32_t)(c.z1 - c.z0 + 2);
-        if (c.h64) {
-            __syncthreads();
-            flush_packed<T, PER>(c);
-        }
     }
     if (c.sh_hist && p.pairs) {
         __syncthreads();
@@ -226,7 +203,14 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
     if (c.sh_hist) {
         __syncthreads();
         for (int i = threadIdx.x; i < p.nd * L; i += kThreads) {
-            const int v = c.sh_hist[i];
+            // global rows are [nd][L]; level L of the interleaved layout is dropped
+            int v;
+            if constexpr (interleaved_hist<DM, SCHED>()) {
+                const int r = i / L, k = i - r * L;
+                v = c.sh_hist[k * dm_nd<DM>() + r];
+            } else {
+                v = c.sh_hist[i];
+            }
             if (v) atomicAdd((unsigned long long *)&p.hist[i], (unsigned long long)(long long)v);
         }
     }
@@ -263,13 +247,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-static size_t smem_bytes(bool tma, int dtype_size, int nd, int L, bool smem_hist, bool has_thr, bool packed,
-                         bool per, bool pairs)
+static size_t smem_bytes(bool tma, int dtype_size, int nd, int L, bool smem_hist, bool has_thr, bool pairs)
 {
     size_t b = tma ? (size_t)NS * FSTRIDE * 4 : 0;
     b += (size_t)NK * KWORDS * 4 + NS * 8 + 16;
-    if (smem_hist) b += ((size_t)nd * L * 4 + 15) & ~(size_t)15;
-    if (smem_hist && packed) b += (size_t)L * 8 + (per ? (((size_t)L * 4 + 15) & ~(size_t)15) : 0);
+    if (smem_hist) b += ((size_t)nd * (L + 1) * 4 + 15) & ~(size_t)15;
     if (smem_hist && pairs) b += ((size_t)4 * (((L + 31) & ~31) + 1) * 4 + 15) & ~(size_t)15;
     if (dtype_size == 1) b += 512;
     else if (has_thr && L <= kThrSmem) b += ((size_t)L * dtype_size + 15) & ~(size_t)15;
@@ -323,9 +305,6 @@ int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, 
     p.nd = ha.rows.nd;
     p.smem_hist = ha.smem_hist;
     p.err = err_flag;
-    // one packed atomic per voxel needs per-item counts below 2^21 per field:
-    // items of at most 64 x 16 x 64 voxels, |change| <= 26 after the offsets
-    p.packed = 0;   // 64-bit shared atomics are not native: one 32-bit atomic per descriptor instead
     p.agg = ha.schedule == 2 ? 1 : 0;
     p.pairs = 0;
     p.uni = nullptr;
@@ -357,8 +336,7 @@ int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, 
         }
     }
     if (ha.schedule == 3 && ha.smem_hist && tma && (desc == 13u || desc == 15u)) p.pairs = 1;
-    const size_t smem = smem_bytes(tma, dsz, p.nd, p.L, p.smem_hist != 0, ba.thr != nullptr, p.packed != 0, per,
-                                   p.pairs != 0);
+    const size_t smem = smem_bytes(tma, dsz, p.nd, p.L, p.smem_hist != 0, ba.thr != nullptr, p.pairs != 0);
     const int items = (int)items64;
     switch (ba.dtype) {
     case EC_F32:

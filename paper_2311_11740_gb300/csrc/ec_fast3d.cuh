@@ -17,7 +17,7 @@ namespace fast3d {
 constexpr int kThreads = 256;
 constexpr int TXF = 64, TYF = 16;           // voxels per plane of a tile
 constexpr int BX = TXF + 8, BY = TYF + 2;   // staged box: x0-4 .. x0+67, y0-1 .. y0+16
-constexpr int KP = 37;                      // key row pitch in 32-bit words (odd: conflict-free rows)
+constexpr int KP = 36;                      // key row pitch in 32-bit words (even: 8-byte row loads)
 constexpr int KWORDS = BY * KP;             // words per key plane
 constexpr int NS = 4;                       // float plane ring depth
 constexpr int NK = 4;                       // key plane ring depth
@@ -37,8 +37,7 @@ struct Params {
     int nd;
     int smem_hist;
     int *err;              // bit 2: a bounded wait gave up
-    const int *uni;        // [0] = 1 if the uniform-spacing guess is exact, [1] = its scale (float bits)
-    int packed;            // 1: one 64-bit shared atomic per voxel, flushed per work item
+    const int *uni;        // [0] = 1 if the uniform-spacing guess is exact, [1], [2] = its scale and offset (float bits)
     int agg;               // 1: warp-aggregated shared-memory updates (lanes grouped by level)
     int pairs;             // 1: two descriptors per 32-bit word, two lane-parity copies (see PairHist)
 };
@@ -93,28 +92,53 @@ __device__ __forceinline__ void tma_load_plane(void *dst, const CUtensorMap *map
 struct FBin {
     const float *t;
     float t0, tl, inv;
+    float off, lm1;   // uniform guess: offset -t0 * inv and L - 1
     int L;
-    int uniform;   // the guess below is always the bin or the bin minus one
+    int uniform;      // the guess below is always the bin or the bin minus one
 };
 
-// Guess of the bin of x from the spacing of the thresholds: the nearest
-// integer to (x - t0) / spacing.  For x in (t_{k-1}, t_k] of near-uniform
-// thresholds this is k-1 or k.  The pre-check kernel and the binning call
-// this same function; explicit round-to-nearest intrinsics keep the two
-// bit-identical.
-__device__ __forceinline__ int bin_guess(float x, float t0, float inv, int L)
+// Parameters of the uniform-spacing guess, from the first and last threshold.
+__device__ __forceinline__ void guess_params(float t0, float tl, int L, float &inv, float &off)
 {
-    const int g = (int)__fmaf_rn(__fsub_rn(x, t0), inv, 0.5f);
-    return min(max(g, 0), L - 1);
+    inv = (L > 1 && tl > t0) ? (float)(L - 1) / (tl - t0) : 0.f;
+    off = -__fmul_rn(t0, inv);
+}
+
+// Guess of the bin of x from the spacing of the thresholds: the nearest
+// integer to x * inv - t0 * inv, clamped to [0, L-1] (NaN lands on L-1).
+// For x in (t_{k-1}, t_k] of near-uniform thresholds this is k-1 or k.  The
+// pre-check and the binning call this same function, with explicit
+// round-to-nearest operations, so the two agree bit for bit.  The rounding
+// adds 1.5 * 2^23, which leaves the integer in the low mantissa bits
+// (exact for 0 <= y < 2^22).
+__device__ __forceinline__ int bin_guess(float x, float inv, float off, float lm1)
+{
+    const float y = fmaxf(fminf(__fmaf_rn(x, inv, off), lm1), 0.f);
+    return __float_as_int(__fadd_rn(y, 12582912.f)) - 0x4B400000;
+}
+
+// Is the guess the bin or the bin minus one for every x whose bin is k?  The
+// guess is monotone in x, so both ends of the level's interval (t_{k-1}, t_k]
+// decide (k = 0: (-inf, t_0]; k = L: the values above t_{L-1}).
+__device__ __forceinline__ bool guess_ok_for_level(const float *t, int L, int k, float inv, float off)
+{
+    const float lm1 = (float)(L - 1);
+    if (k == 0) return t[0] == t[0] && bin_guess(t[0], inv, off, lm1) <= 0;
+    const float lo = t[k - 1];
+    if (lo != lo) return false;
+    if (k == L) return !(lo < INFINITY) || bin_guess(nextafterf(lo, INFINITY), inv, off, lm1) >= L - 1;
+    const float hi = t[k];
+    if (hi != hi) return false;
+    if (!(lo < hi)) return true;   // empty interval
+    return bin_guess(nextafterf(lo, INFINITY), inv, off, lm1) >= k - 1 && bin_guess(hi, inv, off, lm1) <= k;
 }
 
 // Exact bin when the guess is known to be the bin or the bin minus one:
-// one threshold read and one comparison.  NaN -> L.
+// one threshold read and one comparison (NaN: guess L-1, comparison false -> L).
 __device__ __forceinline__ uint32_t fbin_uniform(float x, const FBin &b)
 {
-    const int g = bin_guess(x, b.t0, b.inv, b.L);
-    const int k = g + (x > b.t[g] ? 1 : 0);
-    return x != x ? (uint32_t)b.L : (uint32_t)k;
+    const int g = bin_guess(x, b.inv, b.off, b.lm1);
+    return (uint32_t)(g + (x <= b.t[g] ? 0 : 1));
 }
 
 __device__ __forceinline__ uint32_t bsearch_f(float x, const float *t, int lo, int hi)
@@ -176,14 +200,13 @@ struct Ctx {
     uint32_t *kring;
     uint64_t *bars;
     volatile int *abort_flag;
-    int *sh_hist;
-    unsigned long long *h64;   // packed first-level histogram (EC+13 | area+6 << 21 | count << 42)
-    unsigned int *h32;         // packed perimeter (perimeter + 12)
+    int *sh_hist;              // [nd][L] (run-time rows) or [L+1][nd] (compile-time rows, see zstep)
     uint32_t *pw1, *pw2;       // paired first-level words: [EC | count] and [area | perimeter], 2 copies each
     int pstride;               // words between the two copies (odd multiple of banks apart)
     FBin fb;
     IBin<T> ib;
     int tr, tc;
+    uint32_t bin3;             // third binning share of this thread: float offset | key offset << 16, or ~0
     // current item
     int x0, y0, z0, z1;
     uint32_t base;
@@ -196,31 +219,6 @@ __device__ __forceinline__ uint32_t bin_value(const Ctx<T> &c, T v)
 {
     if constexpr (sizeof(T) == 4) return c.fb.uniform ? fbin_uniform(v, c.fb) : fbin(v, c.fb);
     else return c.ib(v);
-}
-
-constexpr uint64_t kMask21 = (1ull << 21) - 1;
-
-// Move the packed first-level counts into the block's int32 histogram.
-template <typename T, bool PER>
-__device__ __forceinline__ void flush_packed(Ctx<T> &c)
-{
-    const int L = c.p.L;
-    for (int b = threadIdx.x; b < L; b += kThreads) {
-        const unsigned long long v = c.h64[b];
-        if (!v) continue;
-        c.h64[b] = 0ull;
-        const int cnt = (int)(v >> 42);
-        const int ec = (int)(v & kMask21) - 13 * cnt;
-        const int ar = (int)((v >> 21) & kMask21) - 6 * cnt;
-        if (c.p.rows[0] >= 0) c.sh_hist[c.p.rows[0] * L + b] += ec;
-        if (c.p.rows[2] >= 0) c.sh_hist[c.p.rows[2] * L + b] += ar;
-        if (c.p.rows[3] >= 0) c.sh_hist[c.p.rows[3] * L + b] += cnt;
-        if (PER) {
-            const int pe = (int)c.h32[b] - 12 * cnt;
-            c.h32[b] = 0u;
-            if (c.p.rows[1] >= 0) c.sh_hist[c.p.rows[1] * L + b] += pe;
-        }
-    }
 }
 
 // One step of the z walk: bin plane t+z0-1 (if needed), load key plane
@@ -253,24 +251,46 @@ __device__ __forceinline__ void pair_add(uint32_t *word, uint32_t add, int *row_
 template <int DM, int D>
 constexpr int dm_row() { return ((DM & 1) && D > 0) + ((DM & 2) && D > 1) + ((DM & 4) && D > 2); }
 
-// Bin the pairs of one staged float plane into a key plane (3 fixed
-// iterations, the last one partial, so the code is straight-line).
+template <int DM>
+constexpr int dm_nd() { return (DM & 1) + ((DM >> 1) & 1) + ((DM >> 2) & 1) + ((DM >> 3) & 1); }
+
+// Histogram layout of a kernel instantiation: rows interleaved per level
+// ([L+1][nd]) for compile-time rows with one atomic per descriptor.
+template <int DM, int SCHED>
+constexpr bool interleaved_hist() { return DM != 0 && SCHED != 3; }
+
+// Bin the 18 x 34 value pairs of one staged float plane into a key plane.
+// Thread (tr, tc) takes pairs tc and tc + 16 of row tr (fixed offsets, so
+// the addresses are immediates); the 100 pairs left (rows 16-17, pairs 32-33
+// of rows 0-15) go to threads 0-99 through their precomputed offsets.
 template <bool UNI>
-__device__ __forceinline__ void bin_plane_f32(uint32_t *kp, const float *fp, const FBin &fb)
+__device__ __forceinline__ void bin_pair(uint32_t *kp, const float *fp, const FBin &fb)
 {
-#pragma unroll
-    for (int it = 0; it < (kPairsPerPlane + kThreads - 1) / kThreads; it++) {
-        const int i = threadIdx.x + it * kThreads;
-        if (i < kPairsPerPlane) {
-            const int row = i / ((BX - 4) / 2), jp = i - row * ((BX - 4) / 2);
-            const int j = 2 + 2 * jp;
-            const float2 v = *(const float2 *)(fp + row * BX + j);
-            const uint32_t b0 = UNI ? fbin_uniform(v.x, fb) : fbin(v.x, fb);
-            const uint32_t b1 = UNI ? fbin_uniform(v.y, fb) : fbin(v.y, fb);
-            kp[row * KP + (j >> 1)] = b0 | (b1 << 16);
-        }
-    }
+    const float2 v = *(const float2 *)fp;
+    const uint32_t b0 = UNI ? fbin_uniform(v.x, fb) : fbin(v.x, fb);
+    const uint32_t b1 = UNI ? fbin_uniform(v.y, fb) : fbin(v.y, fb);
+    *kp = b0 | (b1 << 16);
 }
+
+template <bool UNI, typename T>
+__device__ __forceinline__ void bin_plane_f32(uint32_t *kp, const float *fp, const Ctx<T> &c)
+{
+    const int fo = c.tr * BX + 2 + 2 * c.tc, ko = c.tr * KP + c.tc;
+    bin_pair<UNI>(kp + ko, fp + fo, c.fb);
+    bin_pair<UNI>(kp + ko + 16, fp + fo + 32, c.fb);
+    if (c.bin3 != ~0u) bin_pair<UNI>(kp + (c.bin3 >> 16), fp + (c.bin3 & 0xFFFFu), c.fb);
+}
+
+// Offsets of a thread's third binning share (see bin_plane_f32).
+__device__ __forceinline__ uint32_t bin3_offsets(int tid)
+{
+    int row, jp;
+    if (tid < 2 * 34) { row = 16 + tid / 34; jp = tid % 34; }
+    else if (tid < 2 * 34 + 32) { row = (tid - 68) >> 1; jp = 32 + ((tid - 68) & 1); }
+    else return ~0u;
+    return (uint32_t)(row * BX + 2 + 2 * jp) | ((uint32_t)(row * KP + jp) << 16);
+}
+static_assert(BY == 18 && (BX - 4) / 2 == 34 && kThreads == 256, "binning shares assume 18 x 34 pairs, 256 threads");
 
 template <typename T, bool TMA, bool PER, int R, int DM, int SCHED = 0>
 __device__ __forceinline__ bool zstep(Ctx<T> &c, const CUtensorMap *tmap, uint32_t (&win)[3][3][5], int t)
@@ -305,12 +325,12 @@ __device__ __forceinline__ bool zstep(Ctx<T> &c, const CUtensorMap *tmap, uint32
             const uint32_t never = (uint32_t)L | ((uint32_t)L << 16);
             for (int i = threadIdx.x; i < kPairsPerPlane; i += kThreads) {
                 const int row = i / ((BX - 4) / 2), jp = i - row * ((BX - 4) / 2);
-                kp[row * KP + 1 + jp] = never;
+                kp[row * KP + jp] = never;
             }
         } else if constexpr (TMA) {
             const float *fp = c.fring + ((c.base + (uint32_t)(pb - (c.z0 - 1))) % NS) * FSTRIDE;
-            if (c.fb.uniform) bin_plane_f32<true>(kp, fp, c.fb);
-            else bin_plane_f32<false>(kp, fp, c.fb);
+            if (c.fb.uniform) bin_plane_f32<true>(kp, fp, c);
+            else bin_plane_f32<false>(kp, fp, c);
         } else {
             const T *f = (const T *)c.p.field;
             const bool zin = true;
@@ -324,7 +344,7 @@ __device__ __forceinline__ bool zstep(Ctx<T> &c, const CUtensorMap *tmap, uint32
                     if (c.interior || (gx >= 0 && gx < c.p.W)) b0 = bin_value(c, rowp[gx]);
                     if (c.interior || (gx + 1 >= 0 && gx + 1 < c.p.W)) b1 = bin_value(c, rowp[gx + 1]);
                 }
-                kp[row * KP + (j >> 1)] = b0 | (b1 << 16);
+                kp[row * KP + jp] = b0 | (b1 << 16);
             }
         }
     }
@@ -334,8 +354,9 @@ __device__ __forceinline__ bool zstep(Ctx<T> &c, const CUtensorMap *tmap, uint32
         constexpr int W = (R + 1) % 3;
 #pragma unroll
         for (int dy = 0; dy < 3; dy++) {
-            const uint32_t *r = kp + (c.tr + dy) * KP + 1 + 2 * c.tc;
-            const uint32_t w0 = r[0], w1 = r[1], w2 = r[2], w3 = r[3];
+            const uint32_t *r = kp + (c.tr + dy) * KP + 2 * c.tc;
+            const uint2 a = *(const uint2 *)r, b = *(const uint2 *)(r + 2);
+            const uint32_t w0 = a.x, w1 = a.y, w2 = b.x, w3 = b.y;
             win[W][dy][0] = w1;
             win[W][dy][1] = w2;
             win[W][dy][2] = __byte_perm(w0, w1, 0x5432);   // keys x-1, x
@@ -389,17 +410,19 @@ __device__ __forceinline__ bool zstep(Ctx<T> &c, const CUtensorMap *tmap, uint32
                 }
                 return true;
             } else {
+                // interleaved rows [L+1][ND]: one address per voxel, the rows at
+                // immediate offsets; the never-active level L has its own
+                // (discarded) slot, so no test is needed
+                constexpr int ND = dm_nd<DM>();
 #pragma unroll
-            for (int v = 0; v < 4; v++) {
-                const uint32_t k = key[v];
-                if (k < (uint32_t)L) {
-                    if (DM & 1) atomicAdd(&h[dm_row<DM, 0>() * L + k], ecv[v]);
-                    if (DM & 2) atomicAdd(&h[dm_row<DM, 1>() * L + k], pev[v]);
-                    if (DM & 4) atomicAdd(&h[dm_row<DM, 2>() * L + k], arv[v]);
-                    if (DM & 8) atomicAdd(&h[dm_row<DM, 3>() * L + k], 1);
+                for (int v = 0; v < 4; v++) {
+                    int *const e = h + key[v] * ND;
+                    if (DM & 1) atomicAdd(e + dm_row<DM, 0>(), ecv[v]);
+                    if (DM & 2) atomicAdd(e + dm_row<DM, 1>(), pev[v]);
+                    if (DM & 4) atomicAdd(e + dm_row<DM, 2>(), arv[v]);
+                    if (DM & 8) atomicAdd(e + dm_row<DM, 3>(), 1);
                 }
-            }
-            return true;
+                return true;
             }
         }
         if constexpr (SCHED == 2) {

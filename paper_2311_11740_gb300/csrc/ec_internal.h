@@ -80,7 +80,7 @@ void row_scales(int ndim, int algo, uint32_t desc, int32_t out[kMaxDesc]);
 
 // Shared-memory budget for the block-private histogram.
 constexpr size_t kSmemHistBudget = 96 * 1024;
-inline bool use_smem_hist(int nd, int32_t L) { return (size_t)nd * (size_t)L * 4 <= kSmemHistBudget; }
+inline bool use_smem_hist(int nd, int32_t L) { return (size_t)nd * ((size_t)L + 1) * 4 <= kSmemHistBudget; }
 
 enum { ALGO_AUTO = 0, ALGO_VOXEL = 1, ALGO_VERTEX = 2 };
 
