@@ -410,7 +410,7 @@ int64_t ec_selfcheck_rules(void)
         return rs;
     };
     for (int trial = 0; trial < 200000; trial++) {
-        const uint32_t span = (trial % 3 == 0) ? 3u : (trial % 3 == 1 ? 40u : 32767u);
+        const uint32_t span = (trial % 3 == 0) ? 3u : (trial % 3 == 1 ? 40u : (uint32_t)kMaxFastL3 + 1u);
         uint32_t k0[27], k1[27];
         for (int i = 0; i < 27; i++) {
             k0[i] = (uint32_t)(rnd() % span);

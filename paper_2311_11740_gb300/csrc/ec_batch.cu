@@ -380,7 +380,7 @@ extern "C" int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, voi
     for (int oi = 0; oi < n; oi++) {
         const ec_field_desc &d = fields[order[oi]];
         if (d.L == 0) continue;
-        if (d.ndim == 3 && d.L > 32767) {
+        if (d.ndim == 3 && d.L > kMaxFastL3) {
             separate.push_back(order[oi]);
             continue;
         }

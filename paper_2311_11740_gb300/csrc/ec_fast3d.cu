@@ -277,12 +277,12 @@ static int launch_t(const CUtensorMap &map, const Params &p, size_t smem, int nu
 }  // namespace fast3d
 
 // Returns EC_ERR_UNSUPPORTED (without launching) when the request does not fit
-// this kernel (more than 32767 levels, or dims beyond 32-bit tile indices).
+// this kernel (more than kMaxFastL3 levels, or dims beyond 32-bit tile indices).
 int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha, int tile_z,
                    int grid_override, int num_sms, int *err_flag, cudaStream_t s, const int zrange[4])
 {
     using namespace fast3d;
-    if (ba.L > 32767 || dims[0] > INT32_MAX / 2 || dims[1] > INT32_MAX / 2 || dims[2] > INT32_MAX / 2)
+    if (ba.L > kMaxFastL3 || dims[0] > INT32_MAX / 2 || dims[1] > INT32_MAX / 2 || dims[2] > INT32_MAX / 2)
         return EC_ERR_UNSUPPORTED;
     Params p{};
     p.field = field;

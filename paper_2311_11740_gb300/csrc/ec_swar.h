@@ -56,6 +56,10 @@ EC_HD uint32_t gather2(uint32_t acc, uint32_t a, uint32_t b)
 
 EC_HD uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (a & c) | (b & c); }
 
+// Largest level count of the 3D paths that use pair_delta: every key,
+// including the never-active level L, fits a 16-bit lane below 0x8000.
+constexpr int kMaxFastL3 = 32767;
+
 struct PairDelta {
     int ec[2], per[2], area[2];
 };
