@@ -403,7 +403,7 @@ int64_t ec_selfcheck_rules(void)
     }
     for (auto &x : th) x.join();
     for (auto v : part) bad += v;
-    // paired 16-bit-lane evaluation (fast kernel) against the scalar closed form
+    // four-voxel byte-mask evaluation (fast kernel) against the scalar closed form
     uint64_t rs = 0x9E3779B97F4A7C15ull;
     auto rnd = [&rs]() {
         rs ^= rs << 13; rs ^= rs >> 7; rs ^= rs << 17;
@@ -411,24 +411,27 @@ int64_t ec_selfcheck_rules(void)
     };
     for (int trial = 0; trial < 200000; trial++) {
         const uint32_t span = (trial % 3 == 0) ? 3u : (trial % 3 == 1 ? 40u : (uint32_t)kMaxFastL3 + 1u);
-        uint32_t k0[27], k1[27];
+        uint32_t k[4][27];
+        for (int v = 0; v < 4; v++)
+            for (int i = 0; i < 27; i++) k[v][i] = (uint32_t)(rnd() % span);
+        uint32_t n0[27], n1[27];
         for (int i = 0; i < 27; i++) {
-            k0[i] = (uint32_t)(rnd() % span);
-            k1[i] = (uint32_t)(rnd() % span);
+            n0[i] = k[0][i] | (k[1][i] << 16);
+            n1[i] = k[2][i] | (k[3][i] << 16);
         }
-        uint32_t n[27];
-        for (int i = 0; i < 27; i++) n[i] = k0[i] | (k1[i] << 16);
-        const PairDelta pd = pair_delta<true>(n, n[13]);
-        for (int v = 0; v < 2; v++) {
-            const uint32_t *k = v ? k1 : k0;
+        const QuadDelta q = quad_delta<true>(n0, n0[13], n1, n1[13]);
+        const int ec[4] = {sbyte<0>(q.ec), sbyte<1>(q.ec), sbyte<2>(q.ec), sbyte<3>(q.ec)};
+        const int pe[4] = {sbyte<0>(q.per), sbyte<1>(q.per), sbyte<2>(q.per), sbyte<3>(q.per)};
+        const int ar[4] = {sbyte<0>(q.area), sbyte<1>(q.area), sbyte<2>(q.area), sbyte<3>(q.area)};
+        for (int v = 0; v < 4; v++) {
             uint32_t P = 0;
             for (int i = 0; i < 27; i++) {
                 if (i == 13) continue;
-                const bool prec = i < 13 ? k[i] <= k[13] : k[i] < k[13];
+                const bool prec = i < 13 ? k[v][i] <= k[v][13] : k[v][i] < k[v][13];
                 P |= (uint32_t)prec << i;
             }
             const Delta3 d = voxel_delta_3d(P);
-            if (pd.ec[v] != d.ec || pd.per[v] != d.per || pd.area[v] != d.area) bad++;
+            if (ec[v] != d.ec || pe[v] != d.per || ar[v] != d.area) bad++;
         }
     }
     return bad;

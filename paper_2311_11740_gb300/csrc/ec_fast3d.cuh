@@ -378,12 +378,11 @@ __device__ __forceinline__ bool zstep(Ctx<T> &c, const CUtensorMap *tmap, uint32
                 n1[i - 1] = w[3]; n1[i] = w[1]; n1[i + 1] = w[4];
             }
         const uint32_t c0 = win[R][1][0], c1 = win[R][1][1];
-        const PairDelta d0 = pair_delta<PER>(n0, c0);
-        const PairDelta d1 = pair_delta<PER>(n1, c1);
+        const QuadDelta q = quad_delta<PER>(n0, c0, n1, c1);
         const uint32_t key[4] = {c0 & 0xFFFFu, c0 >> 16, c1 & 0xFFFFu, c1 >> 16};
-        const int ecv[4] = {d0.ec[0], d0.ec[1], d1.ec[0], d1.ec[1]};
-        const int arv[4] = {d0.area[0], d0.area[1], d1.area[0], d1.area[1]};
-        const int pev[4] = {d0.per[0], d0.per[1], d1.per[0], d1.per[1]};
+        const int ecv[4] = {sbyte<0>(q.ec), sbyte<1>(q.ec), sbyte<2>(q.ec), sbyte<3>(q.ec)};
+        const int arv[4] = {sbyte<0>(q.area), sbyte<1>(q.area), sbyte<2>(q.area), sbyte<3>(q.area)};
+        const int pev[4] = {sbyte<0>(q.per), sbyte<1>(q.per), sbyte<2>(q.per), sbyte<3>(q.per)};
         if constexpr (DM != 0) {
             // descriptor rows fixed at compile time; shared histogram guaranteed
             int *const h = c.sh_hist;
