@@ -169,9 +169,9 @@ __device__ void item_3d(const BField &F, const BItem &it, const Shared &S, const
             for (int e = 0; e < 5; e++) win[a][b][e] = 0;
     const int nsteps = c.z1 - c.z0 + 3;
     for (int t = 0; t < nsteps; t += 3) {
-        zstep<T, false, PER, 0, 0>(c, nullptr, win, t);
-        if (t + 1 < nsteps) zstep<T, false, PER, 1, 0>(c, nullptr, win, t + 1);
-        if (t + 2 < nsteps) zstep<T, false, PER, 2, 0>(c, nullptr, win, t + 2);
+        zstep<T, PER, 0, 0>(c, win, t);
+        if (t + 1 < nsteps) zstep<T, PER, 1, 0>(c, win, t + 1);
+        if (t + 2 < nsteps) zstep<T, PER, 2, 0>(c, win, t + 2);
     }
 }
 

@@ -4,10 +4,10 @@
 // items of `tz` planes.  Per plane:
 //   * float32 fields: the Tensor Memory Accelerator copies a 72 x 18 box of
 //     the plane (x from x0-4 so the start is 16-byte aligned, y from y0-1)
-//     into a 4-deep shared-memory ring, tracked by mbarriers, three planes
-//     ahead of use.  Out-of-bounds elements arrive as NaN, which bins to the
-//     never-active level, exactly what cells outside the field are.  Other
-//     dtypes (or unaligned float32 fields) are read with plain loads.
+//     into an 8-deep shared-memory ring, tracked by mbarriers, about six
+//     planes ahead of use.  Out-of-bounds elements arrive as NaN, which bins
+//     to the never-active level, exactly what cells outside the field are.
+//     Other dtypes (or unaligned float32 fields) are read with plain loads.
 //   * every thread bins pairs of values of the staged plane to 16-bit levels
 //     (a guess from the uniform spacing, checked against the thresholds and
 //     corrected by binary search when it misses) into a 4-deep ring of key
@@ -16,8 +16,10 @@
 //     3 x 3 x 6 key window in registers (sliding along z), compares pairs of
 //     voxels per instruction (ec_swar.h) and adds each voxel's contribution
 //     change at its level to the block's shared-memory histogram.
-// One __syncthreads per plane orders the rings.  Waits on mbarriers are
-// bounded: a wait that gives up sets an error flag and the block returns.
+// The rings are ordered by one __syncthreads per two planes on the TMA path
+// (two planes binned per barrier, three planes ahead of their count) and one
+// per plane with plain loads.  Waits on mbarriers are bounded: a wait that
+// gives up sets an error flag and the block returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -169,20 +171,30 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
         c.interior = c.x0 >= 4 && c.x0 + TXF + 4 <= p.W;
         __syncthreads();   // the previous item is done with both rings
         c.base = seq;
-        if (TMA && threadIdx.x == 0) {
-            for (int q = 0; q < NS - 1; q++) {
-                const int pz = c.z0 - 1 + q;
-                if (pz > c.z1) break;
-                const uint32_t slot = (c.base + q) % NS;
-                mbar_expect_tx(&c.bars[slot], BX * BY * 4);
-                tma_load_plane(c.fring + slot * FSTRIDE, &tmap, c.x0 - 4, c.y0 - 1, pz, &c.bars[slot]);
+        if constexpr (TMA) {
+            // planes z0-1 .. z0+NS-4 now; the barrier steps request the rest
+            if (threadIdx.x == 0) {
+                for (int q = 0; q < NS - 2; q++) {
+                    const int pz = c.z0 - 1 + q;
+                    if (pz > c.z1) break;
+                    const uint32_t slot = (c.base + q) % NS;
+                    mbar_expect_tx(&c.bars[slot], BX * BY * 4);
+                    tma_load_plane(c.fring + slot * FSTRIDE, &tmap, c.x0 - 4, c.y0 - 1, pz, &c.bars[slot]);
+                }
             }
-        }
-        const int nsteps = c.z1 - c.z0 + 3;
-        for (int t = 0; t < nsteps; t += 3) {
-            if (!zstep<T, TMA, PER, 0, DM, SCHED>(c, &tmap, win, t)) return;
-            if (t + 1 < nsteps && !zstep<T, TMA, PER, 1, DM, SCHED>(c, &tmap, win, t + 1)) return;
-            if (t + 2 < nsteps && !zstep<T, TMA, PER, 2, DM, SCHED>(c, &tmap, win, t + 2)) return;
+            const int nsteps = c.z1 - c.z0 + 4;
+            for (int t = 0; t < nsteps; t += 3) {
+                if (!zstep_tma<T, PER, 0, DM, SCHED>(c, &tmap, win, t)) return;
+                if (t + 1 < nsteps && !zstep_tma<T, PER, 1, DM, SCHED>(c, &tmap, win, t + 1)) return;
+                if (t + 2 < nsteps && !zstep_tma<T, PER, 2, DM, SCHED>(c, &tmap, win, t + 2)) return;
+            }
+        } else {
+            const int nsteps = c.z1 - c.z0 + 3;
+            for (int t = 0; t < nsteps; t += 3) {
+                if (!zstep<T, PER, 0, DM, SCHED>(c, win, t)) return;
+                if (t + 1 < nsteps && !zstep<T, PER, 1, DM, SCHED>(c, win, t + 1)) return;
+                if (t + 2 < nsteps && !zstep<T, PER, 2, DM, SCHED>(c, win, t + 2)) return;
+            }
         }
         if (TMA) seq += (uint32_t)(c.z1 - c.z0 + 2);
     }

@@ -19,7 +19,7 @@ constexpr int TXF = 64, TYF = 16;           // voxels per plane of a tile
 constexpr int BX = TXF + 8, BY = TYF + 2;   // staged box: x0-4 .. x0+67, y0-1 .. y0+16
 constexpr int KP = 36;                      // key row pitch in 32-bit words (even: 8-byte row loads)
 constexpr int KWORDS = BY * KP;             // words per key plane
-constexpr int NS = 4;                       // float plane ring depth
+constexpr int NS = 8;                       // float plane ring depth (TMA path)
 constexpr int NK = 4;                       // key plane ring depth
 constexpr int kThrSmem = 4096;
 constexpr int kPairsPerPlane = BY * (BX - 4) / 2;   // key pairs j = 2..69 of 18 rows
@@ -221,9 +221,6 @@ __device__ __forceinline__ uint32_t bin_value(const Ctx<T> &c, T v)
     else return c.ib(v);
 }
 
-// One step of the z walk: bin plane t+z0-1 (if needed), load key plane
-// s+1 into window slot (R+1)%3, and add the contributions of plane s.
-// R = t mod 3 where s = z0 - 3 + t.  Returns false if the block must stop.
 // Paired 16-bit fields in one 32-bit word: value = lo + 65536 * hi with lo a
 // signed 16-bit field (its borrow runs into hi), so any sequence of adds
 // decodes exactly while |lo| and |hi| stay below 2^15.  A thread that sees a
@@ -273,17 +270,30 @@ __device__ __forceinline__ void bin_pair(uint32_t *kp, const float *fp, const FB
 }
 
 template <bool UNI, typename T>
-__device__ __forceinline__ void bin_plane_f32(uint32_t *kp, const float *fp, const Ctx<T> &c)
+__device__ __forceinline__ void bin_plane_f32(uint32_t *kp, const float *fp, const Ctx<T> &c, bool extra)
 {
     const int fo = c.tr * BX + 2 + 2 * c.tc, ko = c.tr * KP + c.tc;
     bin_pair<UNI>(kp + ko, fp + fo, c.fb);
     bin_pair<UNI>(kp + ko + 16, fp + fo + 32, c.fb);
-    if (c.bin3 != ~0u) bin_pair<UNI>(kp + (c.bin3 >> 16), fp + (c.bin3 & 0xFFFFu), c.fb);
+    if (extra && c.bin3 != ~0u) bin_pair<UNI>(kp + (c.bin3 >> 16), fp + (c.bin3 & 0xFFFFu), c.fb);
 }
 
-// Offsets of a thread's third binning share (see bin_plane_f32).
+// Fill a key plane with the never-active level (planes outside the field).
+__device__ __forceinline__ void fill_never(uint32_t *kp, int L)
+{
+    const uint32_t never = (uint32_t)L | ((uint32_t)L << 16);
+    for (int i = threadIdx.x; i < kPairsPerPlane; i += kThreads) {
+        const int row = i / ((BX - 4) / 2), jp = i - row * ((BX - 4) / 2);
+        kp[row * KP + jp] = never;
+    }
+}
+
+// Offsets of a thread's third binning share (see bin_plane_f32): the 100
+// pairs left over go to threads 0-99 in one plane of a barrier step and to
+// threads 128-227 in the other.
 __device__ __forceinline__ uint32_t bin3_offsets(int tid)
 {
+    if (tid >= 128) tid -= 128;
     int row, jp;
     if (tid < 2 * 34) { row = 16 + tid / 34; jp = tid % 34; }
     else if (tid < 2 * 34 + 32) { row = (tid - 68) >> 1; jp = 32 + ((tid - 68) & 1); }
@@ -292,62 +302,12 @@ __device__ __forceinline__ uint32_t bin3_offsets(int tid)
 }
 static_assert(BY == 18 && (BX - 4) / 2 == 34 && kThreads == 256, "binning shares assume 18 x 34 pairs, 256 threads");
 
-template <typename T, bool TMA, bool PER, int R, int DM, int SCHED = 0>
-__device__ __forceinline__ bool zstep(Ctx<T> &c, const CUtensorMap *tmap, uint32_t (&win)[3][3][5], int t)
+// Load key plane s+1 into window slot (R+1)%3 and add the contributions of
+// plane s (R = position of plane s in the 3-plane register window).
+template <typename T, bool PER, int R, int DM, int SCHED>
+__device__ __forceinline__ void count_plane(Ctx<T> &c, uint32_t (&win)[3][3][5], int s)
 {
-    const int s = c.z0 - 3 + t;
-    const int pb = s + 2;
     const int L = c.p.L;
-    if (TMA && threadIdx.x == 0 && pb <= c.z1) {
-        const uint32_t q = (uint32_t)(pb - (c.z0 - 1));
-        const uint32_t slot = (c.base + q) % NS;
-        if (!mbar_wait(&c.bars[slot], (c.parity >> slot) & 1u)) {
-            *c.abort_flag = 1;
-            atomicOr(c.p.err, 4);
-        }
-        c.parity ^= 1u << slot;
-    }
-    __syncthreads();
-    if (*c.abort_flag) return false;
-    if (TMA && threadIdx.x == 0) {
-        const int pi = s + NS + 1;
-        if (pi <= c.z1) {
-            const uint32_t q = (uint32_t)(pi - (c.z0 - 1));
-            const uint32_t slot = (c.base + q) % NS;
-            mbar_expect_tx(&c.bars[slot], BX * BY * 4);
-            tma_load_plane(c.fring + slot * FSTRIDE, tmap, c.x0 - 4, c.y0 - 1, pi, &c.bars[slot]);
-        }
-    }
-    // ---- bin plane pb
-    if (pb <= c.z1) {
-        uint32_t *kp = c.kring + (uint32_t)((pb + 8) % NK) * KWORDS;
-        if (pb < c.p.zv0 || pb >= c.p.zv1) {
-            const uint32_t never = (uint32_t)L | ((uint32_t)L << 16);
-            for (int i = threadIdx.x; i < kPairsPerPlane; i += kThreads) {
-                const int row = i / ((BX - 4) / 2), jp = i - row * ((BX - 4) / 2);
-                kp[row * KP + jp] = never;
-            }
-        } else if constexpr (TMA) {
-            const float *fp = c.fring + ((c.base + (uint32_t)(pb - (c.z0 - 1))) % NS) * FSTRIDE;
-            if (c.fb.uniform) bin_plane_f32<true>(kp, fp, c);
-            else bin_plane_f32<false>(kp, fp, c);
-        } else {
-            const T *f = (const T *)c.p.field;
-            const bool zin = true;
-            for (int i = threadIdx.x; i < kPairsPerPlane; i += kThreads) {
-                const int row = i / ((BX - 4) / 2), jp = i - row * ((BX - 4) / 2);
-                const int j = 2 + 2 * jp;
-                const int64_t gy = (int64_t)c.y0 - 1 + row, gx = (int64_t)c.x0 - 4 + j;
-                uint32_t b0 = (uint32_t)L, b1 = (uint32_t)L;
-                if (zin && gy >= 0 && gy < c.p.H) {
-                    const T *rowp = f + ((int64_t)pb * c.p.H + gy) * c.p.W;
-                    if (c.interior || (gx >= 0 && gx < c.p.W)) b0 = bin_value(c, rowp[gx]);
-                    if (c.interior || (gx + 1 >= 0 && gx + 1 < c.p.W)) b1 = bin_value(c, rowp[gx + 1]);
-                }
-                kp[row * KP + jp] = b0 | (b1 << 16);
-            }
-        }
-    }
     // ---- load key plane s+1 into window slot (R+1)%3
     if (s >= c.z0 - 2) {
         const uint32_t *kp = c.kring + (uint32_t)((s + 1 + 8) % NK) * KWORDS;
@@ -407,7 +367,7 @@ __device__ __forceinline__ bool zstep(Ctx<T> &c, const CUtensorMap *tmap, uint32
                         }
                     }
                 }
-                return true;
+                return;
             } else {
                 // interleaved rows [L+1][ND]: one address per voxel, the rows at
                 // immediate offsets; the never-active level L has its own
@@ -421,7 +381,7 @@ __device__ __forceinline__ bool zstep(Ctx<T> &c, const CUtensorMap *tmap, uint32
                     if (DM & 4) atomicAdd(e + dm_row<DM, 2>(), arv[v]);
                     if (DM & 8) atomicAdd(e + dm_row<DM, 3>(), 1);
                 }
-                return true;
+                return;
             }
         }
         if constexpr (SCHED == 2) {
@@ -448,7 +408,7 @@ __device__ __forceinline__ bool zstep(Ctx<T> &c, const CUtensorMap *tmap, uint32
                     }
                 }
             }
-            return true;
+            return;
         }
 #pragma unroll
         for (int v = 0; v < 4; v++) {
@@ -465,6 +425,101 @@ __device__ __forceinline__ bool zstep(Ctx<T> &c, const CUtensorMap *tmap, uint32
             }
         }
     }
+}
+
+// One step of the z walk with plain loads: bin plane s+2 into the key ring
+// (one barrier per plane), then count plane s.  R = t mod 3, s = z0 - 3 + t.
+// Returns false if the block must stop.
+template <typename T, bool PER, int R, int DM, int SCHED = 0>
+__device__ __forceinline__ bool zstep(Ctx<T> &c, uint32_t (&win)[3][3][5], int t)
+{
+    const int s = c.z0 - 3 + t;
+    const int pb = s + 2;
+    const int L = c.p.L;
+    __syncthreads();
+    if (*c.abort_flag) return false;
+    // ---- bin plane pb
+    if (pb <= c.z1) {
+        uint32_t *kp = c.kring + (uint32_t)((pb + 8) % NK) * KWORDS;
+        if (pb < c.p.zv0 || pb >= c.p.zv1) {
+            fill_never(kp, L);
+        } else {
+            const T *f = (const T *)c.p.field;
+            for (int i = threadIdx.x; i < kPairsPerPlane; i += kThreads) {
+                const int row = i / ((BX - 4) / 2), jp = i - row * ((BX - 4) / 2);
+                const int j = 2 + 2 * jp;
+                const int64_t gy = (int64_t)c.y0 - 1 + row, gx = (int64_t)c.x0 - 4 + j;
+                uint32_t b0 = (uint32_t)L, b1 = (uint32_t)L;
+                if (gy >= 0 && gy < c.p.H) {
+                    const T *rowp = f + ((int64_t)pb * c.p.H + gy) * c.p.W;
+                    if (c.interior || (gx >= 0 && gx < c.p.W)) b0 = bin_value(c, rowp[gx]);
+                    if (c.interior || (gx + 1 >= 0 && gx + 1 < c.p.W)) b1 = bin_value(c, rowp[gx + 1]);
+                }
+                kp[row * KP + jp] = b0 | (b1 << 16);
+            }
+        }
+    }
+    count_plane<T, PER, R, DM, SCHED>(c, win, s);
+    return true;
+}
+
+// One half-step of the TMA z walk (float32 fields), counting plane
+// h = z0 - 4 + t.  Every other half-step (t even) is a barrier step: thread 0
+// waits for the staged float planes h+3 and h+4, the block synchronises,
+// thread 0 requests planes h+NS+1 and h+NS+2 into the ring slots of planes
+// h+1 and h+2 (binned before this barrier), and the block bins planes h+3
+// and h+4.  Every half-step then loads key plane h+1 (binned at least one
+// barrier earlier) and counts plane h.  Key ring: between two barriers the
+// block reads planes h+1, h+2 and writes h+3, h+4: four distinct slots.
+// Returns false if the block must stop.
+template <typename T, bool PER, int R, int DM, int SCHED = 0>
+__device__ __forceinline__ bool zstep_tma(Ctx<T> &c, const CUtensorMap *tmap, uint32_t (&win)[3][3][5], int t)
+{
+    const int h = c.z0 - 4 + t;
+    const int L = c.p.L;
+    if ((t & 1) == 0) {
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int q = 3; q <= 4; q++) {
+                const int pb = h + q;
+                if (pb > c.z1) break;
+                const uint32_t slot = (c.base + (uint32_t)(pb - (c.z0 - 1))) % NS;
+                if (!mbar_wait(&c.bars[slot], (c.parity >> slot) & 1u)) {
+                    *c.abort_flag = 1;
+                    atomicOr(c.p.err, 4);
+                }
+                c.parity ^= 1u << slot;
+            }
+        }
+        __syncthreads();
+        if (*c.abort_flag) return false;
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int q = NS + 1; q <= NS + 2; q++) {
+                const int pi = h + q;
+                if (pi > c.z1) break;
+                const uint32_t slot = (c.base + (uint32_t)(pi - (c.z0 - 1))) % NS;
+                mbar_expect_tx(&c.bars[slot], BX * BY * 4);
+                tma_load_plane(c.fring + slot * FSTRIDE, tmap, c.x0 - 4, c.y0 - 1, pi, &c.bars[slot]);
+            }
+        }
+        // ---- bin planes h+3 (extra pairs on threads 0-99) and h+4 (threads 128-227)
+#pragma unroll
+        for (int q = 3; q <= 4; q++) {
+            const int pb = h + q;
+            if (pb > c.z1) break;
+            uint32_t *kp = c.kring + (uint32_t)((pb + 8) % NK) * KWORDS;
+            if (pb < c.p.zv0 || pb >= c.p.zv1) {
+                fill_never(kp, L);
+            } else {
+                const float *fp = c.fring + ((c.base + (uint32_t)(pb - (c.z0 - 1))) % NS) * FSTRIDE;
+                const bool extra = (q == 3) == (threadIdx.x < 128);
+                if (c.fb.uniform) bin_plane_f32<true>(kp, fp, c, extra);
+                else bin_plane_f32<false>(kp, fp, c, extra);
+            }
+        }
+    }
+    count_plane<T, PER, R, DM, SCHED>(c, win, h);
     return true;
 }
 
