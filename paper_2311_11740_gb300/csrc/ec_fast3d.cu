@@ -322,8 +322,10 @@ int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, 
     p.uni = nullptr;
     if (ba.dtype == EC_F32) {
         p.uni = err_flag + 2;
-        k_uniform_check<<<1, 256, 0, s>>>((const float *)ba.thr, ba.L, err_flag + 2);
-        EC_CUDA(cudaGetLastError());
+        if (!ba.uni_ready) {
+            k_uniform_check<<<1, 256, 0, s>>>((const float *)ba.thr, ba.L, err_flag + 2);
+            EC_CUDA(cudaGetLastError());
+        }
     }
     const bool per = ha.rows.row[1] >= 0;
     uint32_t desc = 0;

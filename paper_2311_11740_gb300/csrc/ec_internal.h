@@ -36,10 +36,15 @@ inline RowMap row_map(uint32_t desc)
 }
 
 // Everything a histogram kernel needs to turn a raw value into its level.
+// Largest level count of the fast paths (paired 16-bit-lane comparisons):
+// every key, including the never-active level L, fits a lane below 0x8000.
+constexpr int kMaxFastL3 = 32767;
+
 struct BinArgs {
     int32_t L;          // number of levels; bin L = never active
     int dtype;          // EC_U8 / EC_U16 / EC_F32
     const void *thr;    // device thresholds (L values of dtype) or nullptr = identity
+    int uni_ready = 0;  // float32: the uniform-spacing check already ran into err_flag[2..4]
 };
 
 // Scratch histogram: int64 [nd][L], zeroed before the kernels run.

@@ -12,8 +12,10 @@
 //
 // Two streams: the side stream fills buffer b (pinned-host copy or the
 // caller's producer), the compute stream waits for it, counts the slab and
-// releases the buffer with an event.  The memory cap bounds the number and
-// height of the buffers.
+// releases the buffer with an event.  With a host field, a slab's two lower
+// planes (the previous slab's top two) are copied on the device from the
+// previous buffer, so every plane crosses the host link once.  The memory
+// cap bounds the number and height of the buffers.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -133,9 +135,14 @@ extern "C" int ec_curve_3d_stream(ec_ctx *ctx, const void *host_field, ec_slab_f
     EC_CUDA(cudaMemsetAsync(base, 0, fixed, res.comp));
     if (thresholds_host)
         EC_CUDA(cudaMemcpyAsync(thr_dev, thresholds_host, (size_t)L * dsz, cudaMemcpyHostToDevice, res.comp));
-    EC_CUDA(cudaStreamSynchronize(res.comp));
 
-    const BinArgs ba{L, dtype, thr_dev};
+    BinArgs ba{L, dtype, thr_dev};
+    if (dtype == EC_F32 && L <= kMaxFastL3) {
+        // one spacing check per call, not per slab
+        rc = launch_uniform_check((const float *)thr_dev, L, flags + 2, res.comp);
+        if (rc) return rc;
+        ba.uni_ready = 1;
+    }
     const HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0, ctx->hist_schedule};
     const int64_t nslabs = (d + S - 1) / S;
     for (int64_t i = 0; i < nslabs; i++) {
@@ -145,10 +152,19 @@ extern "C" int ec_curve_3d_stream(ec_ctx *ctx, const void *host_field, ec_slab_f
         const int64_t n = z1 - z0;   // planes counted; the buffer holds planes z0-1 .. z1
         if (i >= nbuf) EC_CUDA(cudaStreamWaitEvent(res.side, res.freed[b], 0));
         if (host_field) {
-            const int64_t a = std::max<int64_t>(z0 - 1, 0), c = std::min<int64_t>(z1 + 1, d);
-            const char *src = (const char *)host_field + (size_t)a * plane;
-            EC_CUDA(cudaMemcpyAsync(buf + (size_t)(a - (z0 - 1)) * plane, src, (size_t)(c - a) * plane,
-                                    cudaMemcpyHostToDevice, res.side));
+            int64_t a = std::max<int64_t>(z0 - 1, 0);
+            const int64_t c = std::min<int64_t>(z1 + 1, d);
+            if (i > 0) {
+                // planes z0-1 and z0 sit at positions S and S+1 of the previous buffer
+                const char *prev = bufs + (size_t)((i - 1) % nbuf) * buf_bytes;
+                EC_CUDA(cudaMemcpyAsync(buf, prev + (size_t)S * plane, 2 * plane, cudaMemcpyDeviceToDevice, res.side));
+                a = z0 + 1;
+            }
+            if (c > a) {
+                const char *src = (const char *)host_field + (size_t)a * plane;
+                EC_CUDA(cudaMemcpyAsync(buf + (size_t)(a - (z0 - 1)) * plane, src, (size_t)(c - a) * plane,
+                                        cudaMemcpyHostToDevice, res.side));
+            }
         } else {
             const int prc = producer(user, z0 - 1, z1 + 1, buf, (void *)res.side);
             if (prc != 0) { set_error("slab producer failed (%d)", prc); return EC_ERR_ARG; }

@@ -98,10 +98,6 @@ EC_HD int sbyte(uint32_t w)
 
 EC_HD uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (a & c) | (b & c); }
 
-// Largest level count of the 3D paths that use pair_delta: every key,
-// including the never-active level L, fits a 16-bit lane below 0x8000.
-constexpr int kMaxFastL3 = 32767;
-
 // Changes of the four voxels as signed bytes (byte v = voxel v).
 struct QuadDelta {
     uint32_t ec, per, area;
