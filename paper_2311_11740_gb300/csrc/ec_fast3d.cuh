@@ -108,13 +108,15 @@ __device__ __forceinline__ void guess_params(float t0, float tl, int L, float &i
 // integer to x * inv - t0 * inv, clamped to [0, L-1] (NaN lands on L-1).
 // For x in (t_{k-1}, t_k] of near-uniform thresholds this is k-1 or k.  The
 // pre-check and the binning call this same function, with explicit
-// round-to-nearest operations, so the two agree bit for bit.  The rounding
-// adds 1.5 * 2^23, which leaves the integer in the low mantissa bits
-// (exact for 0 <= y < 2^22).
+// round-to-nearest operations, so the two agree bit for bit.  fminf sends
+// NaN to L-1; the saturating round-to-nearest conversion clamps negative
+// values to 0.
 __device__ __forceinline__ int bin_guess(float x, float inv, float off, float lm1)
 {
-    const float y = fmaxf(fminf(__fmaf_rn(x, inv, off), lm1), 0.f);
-    return __float_as_int(__fadd_rn(y, 12582912.f)) - 0x4B400000;
+    const float y = fminf(__fmaf_rn(x, inv, off), lm1);
+    uint32_t g;
+    asm("cvt.rni.sat.u32.f32 %0, %1;" : "=r"(g) : "f"(y));
+    return (int)g;
 }
 
 // Is the guess the bin or the bin minus one for every x whose bin is k?  The
