@@ -403,6 +403,40 @@ int64_t ec_selfcheck_rules(void)
     }
     for (auto &x : th) x.join();
     for (auto v : part) bad += v;
+    // four-pixel byte-mask evaluation (fast 2D kernel) against the scalar closed form
+    {
+        uint64_t r2 = 0x2545F4914F6CDD1Dull;
+        auto rnd2 = [&r2]() {
+            r2 ^= r2 << 13; r2 ^= r2 >> 7; r2 ^= r2 << 17;
+            return r2;
+        };
+        for (int trial = 0; trial < 200000; trial++) {
+            const uint32_t span = (trial % 3 == 0) ? 2u : (trial % 3 == 1 ? 5u : (uint32_t)kMaxFastL3 + 1u);
+            uint32_t k[4][9];
+            for (int v = 0; v < 4; v++)
+                for (int i = 0; i < 9; i++) k[v][i] = (uint32_t)(rnd2() % span);
+            uint32_t n0[9], n1[9];
+            for (int i = 0; i < 9; i++) {
+                n0[i] = k[0][i] | (k[1][i] << 16);
+                n1[i] = k[2][i] | (k[3][i] << 16);
+            }
+            const Quad2 q8 = quad_delta_2d<false>(n0, n0[4], n1, n1[4]);
+            const Quad2 q4 = quad_delta_2d<true>(n0, n0[4], n1, n1[4]);
+            const int e8[4] = {sbyte<0>(q8.ec), sbyte<1>(q8.ec), sbyte<2>(q8.ec), sbyte<3>(q8.ec)};
+            const int e4[4] = {sbyte<0>(q4.ec), sbyte<1>(q4.ec), sbyte<2>(q4.ec), sbyte<3>(q4.ec)};
+            const int pe[4] = {sbyte<0>(q8.per), sbyte<1>(q8.per), sbyte<2>(q8.per), sbyte<3>(q8.per)};
+            for (int v = 0; v < 4; v++) {
+                uint32_t P = 0;
+                for (int i = 0; i < 9; i++) {
+                    if (i == 4) continue;
+                    const bool prec = i < 4 ? k[v][i] <= k[v][4] : k[v][i] < k[v][4];
+                    P |= (uint32_t)prec << i;
+                }
+                const Delta2 d = pixel_delta_2d(P);
+                if (e8[v] != d.ec8 || e4[v] != d.ec4 || pe[v] != d.per) bad++;
+            }
+        }
+    }
     // four-voxel byte-mask evaluation (fast kernel) against the scalar closed form
     uint64_t rs = 0x9E3779B97F4A7C15ull;
     auto rnd = [&rs]() {

@@ -212,12 +212,7 @@ __device__ void item_2d(const BField &F, const BItem &it, const Shared &S, const
     for (int a = 0; a < 3; a++)
 #pragma unroll
         for (int e = 0; e < 5; e++) win[a][e] = 0;
-    const int nsteps = c.y1 - c.y0 + 2;
-    for (int t = 0; t < nsteps; t += 3) {
-        fast2d::ystep<T, CONN4, 0, 0>(c, win, t);
-        if (t + 1 < nsteps) fast2d::ystep<T, CONN4, 1, 0>(c, win, t + 1);
-        if (t + 2 < nsteps) fast2d::ystep<T, CONN4, 2, 0>(c, win, t + 2);
-    }
+    fast2d::walk_item_2d<T, CONN4, 0>(c, win);
 }
 
 // Running sums of one field's histogram into its output (one block).

@@ -38,8 +38,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_pixel2d_fast(Params p)
     c.sh_hist = nullptr;
     if (p.smem_hist) {
         c.sh_hist = (int *)tail;
-        for (int i = threadIdx.x; i < p.nd * L; i += kThreads) c.sh_hist[i] = 0;
-        tail += ((size_t)p.nd * L * 4 + 15) & ~(size_t)15;
+        for (int i = threadIdx.x; i < p.nd * (L + 1); i += kThreads) c.sh_hist[i] = 0;
+        tail += ((size_t)p.nd * (L + 1) * 4 + 15) & ~(size_t)15;
     }
     c.fb = FBin{};
     c.ib = IBin<T>{};
@@ -107,18 +107,19 @@ __global__ void __launch_bounds__(kThreads, 3) k_pixel2d_fast(Params p)
         c.y1 = (int)min((int64_t)c.y0 + p.ry, p.H);
         c.interior = c.x0 >= 2 && c.x0 + SW + 2 <= p.W;
         __syncthreads();   // ring reuse across items
-        // steps t = 0 .. (y1 - y0) + 1: bin rows y0-1 .. y1, count rows y0 .. y1-1
-        const int nsteps = c.y1 - c.y0 + 2;
-        for (int t = 0; t < nsteps; t += 3) {
-            ystep<T, CONN4, 0, DM>(c, win, t);
-            if (t + 1 < nsteps) ystep<T, CONN4, 1, DM>(c, win, t + 1);
-            if (t + 2 < nsteps) ystep<T, CONN4, 2, DM>(c, win, t + 2);
-        }
+        walk_item_2d<T, CONN4, DM>(c, win);
     }
     if (c.sh_hist) {
         __syncthreads();
         for (int i = threadIdx.x; i < p.nd * L; i += kThreads) {
-            const int v = c.sh_hist[i];
+            // global rows are [nd][L]; compile-time rows are interleaved [L+1][nd]
+            int v;
+            if constexpr (DM != 0) {
+                const int r = i / L, k = i - r * L;
+                v = c.sh_hist[k * p.nd + r];
+            } else {
+                v = c.sh_hist[i];
+            }
             if (v) atomicAdd((unsigned long long *)&p.hist[i], (unsigned long long)(long long)v);
         }
     }
@@ -191,7 +192,7 @@ int launch_fast_2d(const void *field, const int64_t dims[2], const BinArgs &ba, 
     }
     const int dsz = ba.dtype == EC_F32 ? 4 : (ba.dtype == EC_U16 ? 2 : 1);
     size_t smem = (size_t)NR * RWORDS * 4;
-    if (p.smem_hist) smem += ((size_t)p.nd * p.L * 4 + 15) & ~(size_t)15;
+    if (p.smem_hist) smem += ((size_t)p.nd * (p.L + 1) * 4 + 15) & ~(size_t)15;
     if (dsz == 1) smem += 512;
     else if (ba.thr && p.L <= kThrSmem) smem += ((size_t)p.L * dsz + 15) & ~(size_t)15;
     const int items = (int)items64;

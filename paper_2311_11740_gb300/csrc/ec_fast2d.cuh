@@ -36,47 +36,6 @@ struct Params {
     const int *uni;
 };
 
-struct Pair2 {
-    int ec[2], per[2];
-};
-
-// Changes of two horizontally adjacent pixels from their 3 x 3 neighbour
-// level pairs n[(dx+1) + 3*(dy+1)] (centre index 4 = the pixels themselves).
-template <bool CONN4>
-__device__ __forceinline__ Pair2 pair_delta_2d(const uint32_t (&n)[9], uint32_t c)
-{
-    const uint32_t cm = c | 0x80008000u;
-    uint32_t d[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++) d[i] = (i == 4) ? 0u : cm - n[i] - (i > 4 ? 0x00010001u : 0u);
-    const uint32_t fxm = d[3], fxp = d[5], fym = d[1], fyp = d[7];
-    const uint32_t cv_mm = fxm | fym | d[0], cv_pm = fxp | fym | d[2];
-    const uint32_t cv_mp = fxm | fyp | d[6], cv_pp = fxp | fyp | d[8];
-    uint32_t pos = 0, neg = 0;
-    pos = gather2<0, 0>(pos, fxm, fxp);
-    pos = gather2<1, 1>(pos, fym, fyp);
-    neg = gather2<0, 0>(neg, cv_mm, cv_pm);
-    neg = gather2<1, 1>(neg, cv_mp, cv_pp);
-    Pair2 r;
-    const int e0 = popc32(pos & 0xFFFFu), e1 = popc32(pos >> 16);
-    r.ec[0] = 1 + e0 - popc32(neg & 0xFFFFu);
-    r.ec[1] = 1 + e1 - popc32(neg >> 16);
-    r.per[0] = 4 - 2 * e0;
-    r.per[1] = 4 - 2 * e1;
-    if (CONN4) {
-        // QD corners: becomes QD when only the diagonal precedes, stops when
-        // exactly the two edge neighbours precede
-        uint32_t qp = 0, qm = 0;
-        qp = gather2<0, 0>(qp, d[0] & ~fxm & ~fym, d[2] & ~fxp & ~fym);
-        qp = gather2<1, 1>(qp, d[6] & ~fxm & ~fyp, d[8] & ~fxp & ~fyp);
-        qm = gather2<0, 0>(qm, fxm & fym & ~d[0], fxp & fym & ~d[2]);
-        qm = gather2<1, 1>(qm, fxm & fyp & ~d[6], fxp & fyp & ~d[8]);
-        r.ec[0] += popc32(qp & 0xFFFFu) - popc32(qm & 0xFFFFu);
-        r.ec[1] += popc32(qp >> 16) - popc32(qm >> 16);
-    }
-    return r;
-}
-
 template <typename T>
 struct Ctx2 {
     Params p;
@@ -95,25 +54,45 @@ __device__ __forceinline__ uint32_t bin_value2(const Ctx2<T> &c, T v)
     else return c.ib(v);
 }
 
-// Bin row y of the strip into ring slot (y mod NR).
+// Raw values of one row share of a thread (words tid, tid+256, tid+512 of
+// the row: pixels x0-2+2w and x0-1+2w), loaded one row step ahead of their
+// binning so that the global-load latency overlaps the counting of a row.
 template <typename T>
-__device__ __forceinline__ void bin_row(Ctx2<T> &c, int64_t y)
+struct RowRaw {
+    T v[3][2];
+    uint32_t ok;   // bit 2*it + j: value v[it][j] lies in the field
+};
+
+template <typename T>
+__device__ __forceinline__ void load_row(const Ctx2<T> &c, int64_t y, RowRaw<T> &r)
 {
-    uint32_t *kr = c.ring + (uint32_t)((y + 8) % NR) * RWORDS;
-    const uint32_t L = (uint32_t)c.p.L;
     const T *f = (const T *)c.p.field;
-    const bool yin = y >= 0 && y < c.p.H;
-    const T *row = f + (yin ? y : 0) * c.p.W;
+    r.ok = 0;
+    if (y < 0 || y >= c.p.H) return;
+    const T *row = f + y * c.p.W;
 #pragma unroll
     for (int it = 0; it < (RWORDS + kThreads - 1) / kThreads; it++) {
         const int w = threadIdx.x + it * kThreads;
         if (w < RWORDS) {
             const int64_t gx = (int64_t)c.x0 - 2 + 2 * w;
-            uint32_t b0 = L, b1 = L;
-            if (yin) {
-                if (c.interior || (gx >= 0 && gx < c.p.W)) b0 = bin_value2(c, row[gx]);
-                if (c.interior || (gx + 1 >= 0 && gx + 1 < c.p.W)) b1 = bin_value2(c, row[gx + 1]);
-            }
+            if (c.interior || (gx >= 0 && gx < c.p.W)) { r.v[it][0] = row[gx]; r.ok |= 1u << (2 * it); }
+            if (c.interior || (gx + 1 >= 0 && gx + 1 < c.p.W)) { r.v[it][1] = row[gx + 1]; r.ok |= 2u << (2 * it); }
+        }
+    }
+}
+
+// Bin a loaded row into ring slot (y mod NR); values outside the field bin to L.
+template <typename T>
+__device__ __forceinline__ void bin_row(Ctx2<T> &c, int64_t y, const RowRaw<T> &r)
+{
+    uint32_t *kr = c.ring + (uint32_t)((y + 8) % NR) * RWORDS;
+    const uint32_t L = (uint32_t)c.p.L;
+#pragma unroll
+    for (int it = 0; it < (RWORDS + kThreads - 1) / kThreads; it++) {
+        const int w = threadIdx.x + it * kThreads;
+        if (w < RWORDS) {
+            const uint32_t b0 = (r.ok >> (2 * it)) & 1u ? bin_value2(c, r.v[it][0]) : L;
+            const uint32_t b1 = (r.ok >> (2 * it)) & 2u ? bin_value2(c, r.v[it][1]) : L;
             kr[w] = b0 | (b1 << 16);
         }
     }
@@ -122,14 +101,16 @@ __device__ __forceinline__ void bin_row(Ctx2<T> &c, int64_t y)
 template <int DM, int D>
 constexpr int dm_row2() { return ((DM & 1) && D > 0) + ((DM & 2) && D > 1); }
 
-// One row step, y = y0 - 2 + t: bin row y+1, then (after the barrier) load
-// it into window slot (R+1)%3 with R = t mod 3, then count row y if it
-// belongs to the item.  Rows y0-1 .. y1 pass through the window.
+// One row step, y = y0 - 2 + t: bin row y+1 (loaded by the previous step),
+// start the loads of row y+2, then (after the barrier) load row y+1 into
+// window slot (R+1)%3 with R = t mod 3 and count row y if it belongs to the
+// item.  Rows y0-1 .. y1 pass through the window.
 template <typename T, bool CONN4, int R, int DM>
-__device__ __forceinline__ void ystep(Ctx2<T> &c, uint32_t (&win)[3][5], int t)
+__device__ __forceinline__ void ystep(Ctx2<T> &c, uint32_t (&win)[3][5], RowRaw<T> &raw, int t)
 {
     const int y = c.y0 - 2 + t;
-    bin_row<T>(c, y + 1);
+    bin_row<T>(c, y + 1, raw);
+    if (y + 2 <= c.y1) load_row<T>(c, y + 2, raw);
     __syncthreads();
     {
         const uint32_t *kr = c.ring + (uint32_t)((y + 1 + 8) % NR) * RWORDS + 2 * threadIdx.x;
@@ -151,33 +132,53 @@ __device__ __forceinline__ void ystep(Ctx2<T> &c, uint32_t (&win)[3][5], int t)
             n1[3 * dy] = w[3]; n1[3 * dy + 1] = w[1]; n1[3 * dy + 2] = w[4];
         }
         const uint32_t c0 = win[R][0], c1 = win[R][1];
-        const Pair2 d0 = pair_delta_2d<CONN4>(n0, c0);
-        const Pair2 d1 = pair_delta_2d<CONN4>(n1, c1);
+        const Quad2 q = quad_delta_2d<CONN4>(n0, c0, n1, c1);
         const uint32_t key[4] = {c0 & 0xFFFFu, c0 >> 16, c1 & 0xFFFFu, c1 >> 16};
-        const int ecv[4] = {d0.ec[0], d0.ec[1], d1.ec[0], d1.ec[1]};
-        const int pev[4] = {d0.per[0], d0.per[1], d1.per[0], d1.per[1]};
+        const int ecv[4] = {sbyte<0>(q.ec), sbyte<1>(q.ec), sbyte<2>(q.ec), sbyte<3>(q.ec)};
+        const int pev[4] = {sbyte<0>(q.per), sbyte<1>(q.per), sbyte<2>(q.per), sbyte<3>(q.per)};
         const int L = c.p.L;
+        if constexpr (DM != 0) {
+            // interleaved rows [L+1][ND] (the never-active level L has its own,
+            // discarded slot): one address per pixel, rows at immediate offsets
+            constexpr int ND = (DM & 1) + ((DM >> 1) & 1) + ((DM >> 2) & 1);
+            int *const h = c.sh_hist;
 #pragma unroll
-        for (int v = 0; v < 4; v++) {
-            const uint32_t k = key[v];
-            if (k >= (uint32_t)L) continue;
-            if constexpr (DM != 0) {
-                int *const h = c.sh_hist;
-                if (DM & 1) atomicAdd(&h[dm_row2<DM, 0>() * L + k], ecv[v]);
-                if (DM & 2) atomicAdd(&h[dm_row2<DM, 1>() * L + k], pev[v]);
-                if (DM & 4) atomicAdd(&h[dm_row2<DM, 2>() * L + k], 1);
-            } else {
+            for (int v = 0; v < 4; v++) {
+                int *const e = h + key[v] * ND;
+                if (DM & 1) atomicAdd(e + dm_row2<DM, 0>(), ecv[v]);
+                if (DM & 2) atomicAdd(e + dm_row2<DM, 1>(), pev[v]);
+                if (DM & 4) atomicAdd(e + dm_row2<DM, 2>(), 1);
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const uint32_t k = key[v];
+                if (k >= (uint32_t)L) continue;
                 const int vals[3] = {ecv[v], pev[v], 1};
 #pragma unroll
-                for (int q = 0; q < 3; q++) {
-                    const int r = c.p.rows[q];
-                    if (r < 0 || vals[q] == 0) continue;
-                    if (c.sh_hist) atomicAdd(&c.sh_hist[r * L + k], vals[q]);
+                for (int q2 = 0; q2 < 3; q2++) {
+                    const int r = c.p.rows[q2];
+                    if (r < 0 || vals[q2] == 0) continue;
+                    if (c.sh_hist) atomicAdd(&c.sh_hist[r * L + k], vals[q2]);
                     else atomicAdd((unsigned long long *)&c.p.hist[(size_t)r * L + k],
-                                   (unsigned long long)(long long)vals[q]);
+                                   (unsigned long long)(long long)vals[q2]);
                 }
             }
         }
+    }
+}
+
+// Walk one item: rows y0-1 .. y1 are binned, rows y0 .. y1-1 counted.
+template <typename T, bool CONN4, int DM>
+__device__ __forceinline__ void walk_item_2d(Ctx2<T> &c, uint32_t (&win)[3][5])
+{
+    RowRaw<T> raw;
+    load_row<T>(c, c.y0 - 1, raw);
+    const int nsteps = c.y1 - c.y0 + 2;
+    for (int t = 0; t < nsteps; t += 3) {
+        ystep<T, CONN4, 0, DM>(c, win, raw, t);
+        if (t + 1 < nsteps) ystep<T, CONN4, 1, DM>(c, win, raw, t + 1);
+        if (t + 2 < nsteps) ystep<T, CONN4, 2, DM>(c, win, raw, t + 2);
     }
 }
 

@@ -35,34 +35,6 @@
 namespace ec {
 
 // prmt.b32 in its default mode with all four selector nibbles asking for
-// sign replication: output bytes = msb of (a.byte1, b.byte1, a.byte3, b.byte3)
-// replicated over 8 bits, i.e. the lane-0 and lane-1 comparison bits of a and b
-// (the 2D kernel gathers pixel pairs this way).
-EC_HD uint32_t sign_bytes(uint32_t a, uint32_t b)
-{
-#if defined(__CUDA_ARCH__)
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(0xFBD9u));
-    return d;
-#else
-    const uint32_t m0 = (a >> 15) & 1u ? 0xFFu : 0u;
-    const uint32_t m1 = (b >> 15) & 1u ? 0xFFu : 0u;
-    const uint32_t m2 = (a >> 31) & 1u ? 0xFFu : 0u;
-    const uint32_t m3 = (b >> 31) & 1u ? 0xFFu : 0u;
-    return m0 | (m1 << 8) | (m2 << 16) | (m3 << 24);
-#endif
-}
-
-// Add the comparison bits of words a and b to a per-pixel bit set: pixel 0
-// gets them at bits pa and 8+pb, pixel 1 at 16+pa and 24+pb.
-template <int PA, int PB>
-EC_HD uint32_t gather2(uint32_t acc, uint32_t a, uint32_t b)
-{
-    constexpr uint32_t K = (1u << PA) | (1u << (8 + PB)) | (1u << (16 + PA)) | (1u << (24 + PB));
-    return acc | (sign_bytes(a, b) & K);
-}
-
-// prmt.b32 in its default mode with all four selector nibbles asking for
 // sign replication: output byte v = msb of (a.byte1, a.byte3, b.byte1,
 // b.byte3) replicated over 8 bits, i.e. the comparison bits of voxels
 // 0, 1 (word a) and 2, 3 (word b).
@@ -158,6 +130,47 @@ EC_HD QuadDelta quad_delta(const uint32_t (&n0)[27], uint32_t c0, const uint32_t
         q.per = 0u;
     }
 #undef ECB
+    return q;
+}
+
+// Changes of four horizontally adjacent pixels as signed bytes (byte v =
+// pixel v), from the 3 x 3 neighbour level pairs of the pixel pairs (0, 1)
+// and (2, 3): n0/n1[(dx+1) + 3*(dy+1)] (index 4 = the pixels themselves).
+// Same byte-mask counting as quad_delta.
+struct Quad2 {
+    uint32_t ec, per;
+};
+
+template <bool CONN4>
+EC_HD Quad2 quad_delta_2d(const uint32_t (&n0)[9], uint32_t c0, const uint32_t (&n1)[9],
+                                               uint32_t c1)
+{
+    const uint32_t cm0 = c0 | 0x80008000u, cm1 = c1 | 0x80008000u;
+    uint32_t b[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const uint32_t k = i > 4 ? 0x00010001u : 0u;
+        b[i] = (i == 4) ? 0u : sign_bytes4(cm0 - n0[i] - k, cm1 - n1[i] - k);
+    }
+    const uint32_t fxm = b[3], fxp = b[5], fym = b[1], fyp = b[7];
+    // corner covers: a corner of the pixel is present iff one of its 3 other pixels precedes
+    const uint32_t cv_mm = fxm | fym | b[0], cv_pm = fxp | fym | b[2];
+    const uint32_t cv_mp = fxm | fyp | b[6], cv_pp = fxp | fyp | b[8];
+    const uint32_t sE = (fxm + fxp) + (fym + fyp);
+    uint32_t neg = (cv_mm + cv_pm) + (cv_mp + cv_pp);   // digits subtracted from EC
+    if (CONN4) {
+        // QD corners: a corner becomes QD when only the diagonal precedes and
+        // stops being QD when exactly the two edge neighbours precede
+        const uint32_t qp = ((b[0] & ~fxm & ~fym) + (b[2] & ~fxp & ~fym)) + ((b[6] & ~fxm & ~fyp) + (b[8] & ~fxp & ~fyp));
+        const uint32_t qm = ((fxm & fym & ~b[0]) + (fxp & fym & ~b[2])) + ((fxm & fyp & ~b[6]) + (fxp & fyp & ~b[8]));
+        neg = neg + qm - qp;
+    }
+    // x * 0x01010101 = -x / 255 (mod 2^32).  EC change 1 + nE - nV (+ QD terms)
+    // in [-7, 9], perimeter change 4 - 2 nE in [-4, 4]: each byte gets 128 +
+    // its change, then loses the 128.
+    Quad2 q;
+    q.ec = ((neg - sE) * 0x01010101u + 0x81818181u) ^ 0x80808080u;
+    q.per = (sE * 0x02020202u + 0x84848484u) ^ 0x80808080u;
     return q;
 }
 
