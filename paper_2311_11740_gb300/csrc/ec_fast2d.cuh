@@ -21,6 +21,16 @@ constexpr int SW = 1024;               // pixels per strip
 constexpr int RWORDS = (SW + 4) / 2;   // key words per row: x0-2 .. x0+SW+1
 constexpr int NR = 4;                  // ring rows
 constexpr int kThrSmem = 4096;
+constexpr int KA = 3;                  // raw rows copied ahead (asynchronous path)
+constexpr int NRAW = KA + 2;           // raw row ring: row being binned, row waited for, KA in flight
+
+// Raw row of the asynchronous path: the strip's pixels x0-A .. x0+SW+A-1
+// with A elements (16 bytes) of halo on each side, so that every 16-byte
+// chunk starts aligned.
+template <typename T>
+constexpr int raw_pad() { return 16 / (int)sizeof(T); }
+template <typename T>
+constexpr int raw_bytes() { return (SW + 2 * raw_pad<T>()) * (int)sizeof(T); }
 
 struct Params {
     const void *field;
@@ -40,6 +50,7 @@ template <typename T>
 struct Ctx2 {
     Params p;
     uint32_t *ring;
+    unsigned char *raw;   // raw row ring (asynchronous path)
     int *sh_hist;
     FBin fb;
     IBin<T> ib;
@@ -57,6 +68,8 @@ __device__ __forceinline__ uint32_t bin_value2(const Ctx2<T> &c, T v)
 // Raw values of one row share of a thread (words tid, tid+256, tid+512 of
 // the row: pixels x0-2+2w and x0-1+2w), loaded one row step ahead of their
 // binning so that the global-load latency overlaps the counting of a row.
+// The loads go through the read-only path (the field is never written by
+// the kernel), which the row barrier does not have to wait for.
 template <typename T>
 struct RowRaw {
     T v[3][2];
@@ -75,8 +88,8 @@ __device__ __forceinline__ void load_row(const Ctx2<T> &c, int64_t y, RowRaw<T> 
         const int w = threadIdx.x + it * kThreads;
         if (w < RWORDS) {
             const int64_t gx = (int64_t)c.x0 - 2 + 2 * w;
-            if (c.interior || (gx >= 0 && gx < c.p.W)) { r.v[it][0] = row[gx]; r.ok |= 1u << (2 * it); }
-            if (c.interior || (gx + 1 >= 0 && gx + 1 < c.p.W)) { r.v[it][1] = row[gx + 1]; r.ok |= 2u << (2 * it); }
+            if (c.interior || (gx >= 0 && gx < c.p.W)) { r.v[it][0] = __ldg(row + gx); r.ok |= 1u << (2 * it); }
+            if (c.interior || (gx + 1 >= 0 && gx + 1 < c.p.W)) { r.v[it][1] = __ldg(row + gx + 1); r.ok |= 2u << (2 * it); }
         }
     }
 }
@@ -101,17 +114,11 @@ __device__ __forceinline__ void bin_row(Ctx2<T> &c, int64_t y, const RowRaw<T> &
 template <int DM, int D>
 constexpr int dm_row2() { return ((DM & 1) && D > 0) + ((DM & 2) && D > 1); }
 
-// One row step, y = y0 - 2 + t: bin row y+1 (loaded by the previous step),
-// start the loads of row y+2, then (after the barrier) load row y+1 into
-// window slot (R+1)%3 with R = t mod 3 and count row y if it belongs to the
-// item.  Rows y0-1 .. y1 pass through the window.
+// Load row y+1 into window slot (R+1)%3 (R = position of row y) and count
+// row y if it belongs to the item.
 template <typename T, bool CONN4, int R, int DM>
-__device__ __forceinline__ void ystep(Ctx2<T> &c, uint32_t (&win)[3][5], RowRaw<T> &raw, int t)
+__device__ __forceinline__ void count_row(Ctx2<T> &c, uint32_t (&win)[3][5], int y)
 {
-    const int y = c.y0 - 2 + t;
-    bin_row<T>(c, y + 1, raw);
-    if (y + 2 <= c.y1) load_row<T>(c, y + 2, raw);
-    __syncthreads();
     {
         const uint32_t *kr = c.ring + (uint32_t)((y + 1 + 8) % NR) * RWORDS + 2 * threadIdx.x;
         const uint2 a = *(const uint2 *)kr, b = *(const uint2 *)(kr + 2);
@@ -168,6 +175,89 @@ __device__ __forceinline__ void ystep(Ctx2<T> &c, uint32_t (&win)[3][5], RowRaw<
     }
 }
 
+// One row step, y = y0 - 2 + t: bin row y+1 (loaded by the previous step),
+// start the loads of row y+2, then (after the barrier) load row y+1 into
+// window slot (R+1)%3 with R = t mod 3 and count row y if it belongs to the
+// item.  Rows y0-1 .. y1 pass through the window.
+template <typename T, bool CONN4, int R, int DM>
+__device__ __forceinline__ void ystep(Ctx2<T> &c, uint32_t (&win)[3][5], RowRaw<T> &raw, int t)
+{
+    const int y = c.y0 - 2 + t;
+    bin_row<T>(c, y + 1, raw);
+    if (y + 2 <= c.y1) load_row<T>(c, y + 2, raw);
+    __syncthreads();
+    count_row<T, CONN4, R, DM>(c, win, y);
+}
+
+// ---- asynchronous path: rows copied to shared memory KA rows ahead with
+// cp.async (16-byte chunks, zero-filled outside the field); used when every
+// row starts 16-byte aligned.
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Start this thread's copies of row y (empty if y is beyond the item) and
+// close them as one group.  The row width and start are multiples of 16
+// bytes, so a chunk lies wholly inside or wholly outside the field.
+template <typename T>
+__device__ __forceinline__ void copy_row(const Ctx2<T> &c, int64_t y, bool wanted)
+{
+    constexpr int A = raw_pad<T>(), NCH = raw_bytes<T>() / 16;
+    if (wanted) {
+        unsigned char *slot = c.raw + (uint32_t)((y + 16) % NRAW) * raw_bytes<T>();
+        const bool yin = y >= 0 && y < c.p.H;
+        const T *base = (const T *)c.p.field;
+        for (int q = threadIdx.x; q < NCH; q += kThreads) {
+            const int64_t x = (int64_t)c.x0 - A + (int64_t)q * A;
+            const bool in = yin && x >= 0 && x < c.p.W;
+            cp_async16(fast3d::smem_u32(slot + q * 16), in ? base + y * c.p.W + x : base, in ? 16u : 0u);
+        }
+    }
+    cp_async_commit();
+}
+
+// Bin row y from its raw slot into ring slot (y mod NR); pixels outside the
+// field bin to L.
+template <typename T>
+__device__ __forceinline__ void bin_row_raw(Ctx2<T> &c, int64_t y)
+{
+    constexpr int A = raw_pad<T>();
+    uint32_t *kr = c.ring + (uint32_t)((y + 8) % NR) * RWORDS;
+    const T *raw = (const T *)(c.raw + (uint32_t)((y + 16) % NRAW) * raw_bytes<T>());
+    const uint32_t L = (uint32_t)c.p.L;
+    const bool yin = y >= 0 && y < c.p.H;
+#pragma unroll
+    for (int it = 0; it < (RWORDS + kThreads - 1) / kThreads; it++) {
+        const int w = threadIdx.x + it * kThreads;
+        if (w < RWORDS) {
+            const int64_t gx = (int64_t)c.x0 - 2 + 2 * w;
+            const int ri = 2 * w - 2 + A;
+            const uint32_t b0 = (yin && (c.interior || (gx >= 0 && gx < c.p.W))) ? bin_value2(c, raw[ri]) : L;
+            const uint32_t b1 = (yin && (c.interior || (gx + 1 >= 0 && gx + 1 < c.p.W))) ? bin_value2(c, raw[ri + 1]) : L;
+            kr[w] = b0 | (b1 << 16);
+        }
+    }
+}
+
+// Asynchronous row step, y = y0 - 2 + t: bin row y+1 (its copies finished
+// before the previous barrier), start the copies of row y+2+KA, wait for
+// this thread's copies of row y+2, synchronise, then count as ystep does.
+template <typename T, bool CONN4, int R, int DM>
+__device__ __forceinline__ void ystep_async(Ctx2<T> &c, uint32_t (&win)[3][5], int t)
+{
+    const int y = c.y0 - 2 + t;
+    bin_row_raw<T>(c, y + 1);
+    copy_row<T>(c, y + 2 + KA, y + 2 + KA <= c.y1);
+    cp_async_wait<KA>();
+    __syncthreads();
+    count_row<T, CONN4, R, DM>(c, win, y);
+}
+
 // Walk one item: rows y0-1 .. y1 are binned, rows y0 .. y1-1 counted.
 template <typename T, bool CONN4, int DM>
 __device__ __forceinline__ void walk_item_2d(Ctx2<T> &c, uint32_t (&win)[3][5])
@@ -180,6 +270,22 @@ __device__ __forceinline__ void walk_item_2d(Ctx2<T> &c, uint32_t (&win)[3][5])
         if (t + 1 < nsteps) ystep<T, CONN4, 1, DM>(c, win, raw, t + 1);
         if (t + 2 < nsteps) ystep<T, CONN4, 2, DM>(c, win, raw, t + 2);
     }
+}
+
+// Asynchronous walk of one item (same rows as walk_item_2d).
+template <typename T, bool CONN4, int DM>
+__device__ __forceinline__ void walk_item_2d_async(Ctx2<T> &c, uint32_t (&win)[3][5])
+{
+    for (int q = 0; q <= KA; q++) copy_row<T>(c, c.y0 - 1 + q, c.y0 - 1 + q <= c.y1);
+    cp_async_wait<KA>();
+    __syncthreads();
+    const int nsteps = c.y1 - c.y0 + 2;
+    for (int t = 0; t < nsteps; t += 3) {
+        ystep_async<T, CONN4, 0, DM>(c, win, t);
+        if (t + 1 < nsteps) ystep_async<T, CONN4, 1, DM>(c, win, t + 1);
+        if (t + 2 < nsteps) ystep_async<T, CONN4, 2, DM>(c, win, t + 2);
+    }
+    cp_async_wait<0>();
 }
 
 }  // namespace fast2d

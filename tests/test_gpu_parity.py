@@ -108,6 +108,51 @@ def test_random_2d(ctx, shape, dtype):
         check(ctx, f, thr, L, conn=conn)
 
 
+# Rows whose start is 16-byte aligned go through the asynchronous row copies
+# (whole 16-byte chunks, zero-filled outside the field); the others through
+# per-pixel loads.  Wide fields cover several 1024-pixel strips, the last one
+# partial; heights 1-3 leave items shorter than the copy-ahead distance.
+SHAPES2_WIDE = [(1, 1024), (2, 1040), (3, 2064), (33, 1536), (5, 1041), (4, 1030), (70, 1088)]
+
+
+@pytest.mark.parametrize("shape", SHAPES2_WIDE)
+@pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
+def test_wide_2d_strips(ctx, shape, dtype):
+    rng = np.random.default_rng(zlib.crc32(repr((shape, dtype, "wide")).encode()))
+    smooth = workloads.grf_2d(int(rng.integers(1 << 30)), shape[0], shape[1], 4.0).numpy()
+    if dtype == "u8":
+        f, L, thr = workloads.quantize_u8(torch.from_numpy(smooth)).numpy(), 256, None
+    elif dtype == "u16":
+        f, L, thr = (np.clip(smooth * 400 + 2000, 0, 4000)).astype(np.uint16), 4001, None
+    else:
+        f = smooth.astype(np.float32)
+        L = 257
+        thr = np.linspace(f.min(), f.max(), L).astype(np.float32)
+    for conn in (8, 4):
+        check(ctx, f, thr, L, conn=conn, algos=[ec.ALGO_VOXEL])
+
+
+def test_2d_unaligned_field_pointer(ctx):
+    # a field whose storage starts one element past an aligned address
+    rng = np.random.default_rng(5)
+    for dtype, L in ((torch.uint8, 256), (torch.float32, 100)):
+        h, w = 9, 2048
+        flat = torch.zeros(h * w + 1, dtype=dtype)
+        if dtype == torch.uint8:
+            vals = torch.from_numpy(rng.integers(0, 256, size=h * w).astype(np.uint8))
+            thr = None
+        else:
+            vals = torch.from_numpy(rng.normal(size=h * w).astype(np.float32))
+            thr = np.sort(rng.normal(size=L)).astype(np.float32)
+        flat[1:] = vals
+        dev = flat.cuda()[1:].view(h, w)
+        assert dev.data_ptr() % 16 != 0
+        want = oracle.ec_curves(vals.view(h, w).numpy(), thr, L, 8, ALL2)
+        got = ec.curve(dev, to_dev(thr), L=L, connectivity=8, descriptors=ALL2, ctx=ctx)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(got.cpu().numpy(), want)
+
+
 def test_float_special_values(ctx):
     rng = np.random.default_rng(9)
     f = rng.normal(size=(9, 10, 11)).astype(np.float32)
