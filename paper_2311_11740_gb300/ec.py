@@ -105,6 +105,9 @@ def dtype_code(t) -> int:
     return _TORCH_CODES[t.dtype]
 
 
+_NP_DTYPES = {EC_U8: np.uint8, EC_U16: np.uint16, EC_F32: np.float32}
+
+
 def n_rows(descriptors: int) -> int:
     return bin(descriptors & 0xF).count("1")
 
@@ -268,8 +271,14 @@ class Server:
         self._keep = {}
 
     def submit(self, field, thresholds=None, L=None, connectivity=None, descriptors=EC_DESC_EC):
+        """field: host numpy array or CPU torch tensor (page-locked memory
+        overlaps the copies); thresholds: host array of the field's dtype."""
+        if hasattr(field, "data_ptr"):
+            field = field.contiguous()
         if thresholds is not None:
-            thresholds = np.ascontiguousarray(thresholds, dtype=field.dtype)
+            if hasattr(thresholds, "data_ptr"):
+                thresholds = thresholds.contiguous().numpy()
+            thresholds = np.ascontiguousarray(thresholds, dtype=_NP_DTYPES[dtype_code(field)])
             L = thresholds.size if L is None else L
         out = np.zeros((n_rows(descriptors), L), dtype=np.int64)
         d = _desc(field, thresholds, L, connectivity, descriptors, out)

@@ -46,6 +46,17 @@ def test_served_mix_equals_standalone_and_oracle(ctx):
     sv.close()
 
 
+def test_served_pinned_torch_fields(ctx):
+    # page-locked torch fields with numpy thresholds, as a serving front end passes them
+    reqs = _requests(12, seed=9)
+    sv = ec.Server(device_mem_budget=256 << 20, max_slots=4, ctx=ctx)
+    tickets = [sv.submit(torch.from_numpy(f).pin_memory(), thr, L=L, descriptors=d) for f, thr, L, d in reqs]
+    for t, (f, thr, L, d) in zip(tickets, reqs):
+        np.testing.assert_array_equal(sv.wait(t, timeout_ms=120000),
+                                      oracle.ec_curves(f, thr, L, 8 if f.ndim == 2 else 26, d))
+    sv.close()
+
+
 def test_admission_budget_slots_and_failures(ctx):
     big = workloads.config3(n=160, nblobs=50, L=300)
     f, thr = big[0].numpy(), big[1].numpy()
