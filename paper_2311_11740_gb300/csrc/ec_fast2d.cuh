@@ -193,13 +193,9 @@ __device__ __forceinline__ void ystep(Ctx2<T> &c, uint32_t (&win)[3][5], RowRaw<
 // cp.async (16-byte chunks, zero-filled outside the field); used when every
 // row starts 16-byte aligned.
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+using fast3d::cp_async16;
+using fast3d::cp_async_commit;
+using fast3d::cp_async_wait;
 
 // Start this thread's copies of row y (empty if y is beyond the item) and
 // close them as one group.  The row width and start are multiples of 16

@@ -59,17 +59,29 @@ __global__ void k_uniform_check(const float *t, int L, int *uni)
 #define EC_FAST_MIN_BLOCKS 3
 #endif
 
-template <typename T, bool TMA, bool PER, int DM, int SCHED = 0>
+// Staging modes of the fast 3D kernel.
+enum { MODE_PLAIN = 0, MODE_TMA = 1, MODE_ASYNC = 2 };
+
+template <typename T>
+constexpr size_t stage_bytes(int mode)
+{
+    return mode == MODE_TMA ? (size_t)NS * FSTRIDE * sizeof(float)
+                            : (mode == MODE_ASYNC ? ((size_t)NRAWP * rplane_bytes<T>() + 127) / 128 * 128 : 0);
+}
+
+template <typename T, int MODE, bool PER, int DM, int SCHED = 0>
 __global__ void __launch_bounds__(kThreads, EC_FAST_MIN_BLOCKS)
 k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
 {
+    constexpr bool TMA = MODE == MODE_TMA;
     extern __shared__ __align__(128) unsigned char smem[];
-    // layout: [float ring NS*FSTRIDE*4 (TMA only)] [key ring NK*KWORDS*4] [mbar NS*8] [abort 16]
-    //         [hist nd*(L+1)*4] [thresholds / byte table]
+    // layout: [float ring NS*FSTRIDE*4 (TMA) | raw plane ring (ASYNC)] [key ring NK*KWORDS*4] [mbar NS*8]
+    //         [abort 16] [hist nd*(L+1)*4] [thresholds / byte table]
     Ctx<T> c;
     c.p = p;
-    const size_t fbytes = TMA ? (size_t)NS * FSTRIDE * sizeof(float) : 0;
+    const size_t fbytes = stage_bytes<T>(MODE);
     c.fring = (float *)smem;
+    c.raw = smem;
     c.kring = (uint32_t *)(smem + fbytes);
     c.bars = (uint64_t *)(smem + fbytes + (size_t)NK * KWORDS * 4);
     c.abort_flag = (volatile int *)(c.bars + NS);
@@ -188,6 +200,17 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
                 if (t + 1 < nsteps && !zstep_tma<T, PER, 1, DM, SCHED>(c, &tmap, win, t + 1)) return;
                 if (t + 2 < nsteps && !zstep_tma<T, PER, 2, DM, SCHED>(c, &tmap, win, t + 2)) return;
             }
+        } else if constexpr (MODE == MODE_ASYNC) {
+            for (int q = 0; q < KAP; q++) copy_plane<T>(c, c.z0 - 1 + q, c.z0 - 1 + q <= c.z1);
+            const int nsteps = c.z1 - c.z0 + 3;
+            bool ok = true;
+            for (int t = 0; ok && t < nsteps; t += 3) {
+                ok = zstep_async<T, PER, 0, DM, SCHED>(c, win, t);
+                if (ok && t + 1 < nsteps) ok = zstep_async<T, PER, 1, DM, SCHED>(c, win, t + 1);
+                if (ok && t + 2 < nsteps) ok = zstep_async<T, PER, 2, DM, SCHED>(c, win, t + 2);
+            }
+            cp_async_wait<0>();
+            if (!ok) return;
         } else {
             const int nsteps = c.z1 - c.z0 + 3;
             for (int t = 0; t < nsteps; t += 3) {
@@ -259,9 +282,10 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-static size_t smem_bytes(bool tma, int dtype_size, int nd, int L, bool smem_hist, bool has_thr, bool pairs)
+template <typename T>
+static size_t smem_bytes(int mode, int dtype_size, int nd, int L, bool smem_hist, bool has_thr, bool pairs)
 {
-    size_t b = tma ? (size_t)NS * FSTRIDE * 4 : 0;
+    size_t b = stage_bytes<T>(mode);
     b += (size_t)NK * KWORDS * 4 + NS * 8 + 16;
     if (smem_hist) b += ((size_t)nd * (L + 1) * 4 + 15) & ~(size_t)15;
     if (smem_hist && pairs) b += ((size_t)4 * (((L + 31) & ~31) + 1) * 4 + 15) & ~(size_t)15;
@@ -270,11 +294,11 @@ static size_t smem_bytes(bool tma, int dtype_size, int nd, int L, bool smem_hist
     return b;
 }
 
-template <typename T, bool TMA, bool PER, int DM = 0, int SCHED = 0>
+template <typename T, int MODE, bool PER, int DM = 0, int SCHED = 0>
 static int launch_t(const CUtensorMap &map, const Params &p, size_t smem, int num_sms, int items, int grid_override,
                     cudaStream_t s)
 {
-    auto kern = k_voxel3d_fast<T, TMA, PER, DM, SCHED>;
+    auto kern = k_voxel3d_fast<T, MODE, PER, DM, SCHED>;
     EC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
@@ -284,6 +308,23 @@ static int launch_t(const CUtensorMap &map, const Params &p, size_t smem, int nu
     kern<<<grid, kThreads, smem, s>>>(map, p);
     EC_CUDA(cudaGetLastError());
     return EC_OK;
+}
+
+// Plain-load and cp.async modes: compile-time histogram rows for the common
+// descriptor sets on the cp.async path, run-time rows otherwise.
+template <typename T, int MODE>
+static int launch_loads(const CUtensorMap &map, const Params &p, uint32_t desc, bool per, size_t smem, int num_sms,
+                        int items, int grid_override, cudaStream_t s)
+{
+    if constexpr (MODE == MODE_ASYNC) {
+        if (p.smem_hist) {
+            if (desc == 1u) return launch_t<T, MODE, false, 1>(map, p, smem, num_sms, items, grid_override, s);
+            if (desc == 13u) return launch_t<T, MODE, false, 13>(map, p, smem, num_sms, items, grid_override, s);
+            if (desc == 15u) return launch_t<T, MODE, true, 15>(map, p, smem, num_sms, items, grid_override, s);
+        }
+    }
+    return per ? launch_t<T, MODE, true>(map, p, smem, num_sms, items, grid_override, s)
+               : launch_t<T, MODE, false>(map, p, smem, num_sms, items, grid_override, s);
 }
 
 }  // namespace fast3d
@@ -350,33 +391,41 @@ int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, 
         }
     }
     if (ha.schedule == 3 && ha.smem_hist && tma && (desc == 13u || desc == 15u)) p.pairs = 1;
-    const size_t smem = smem_bytes(tma, dsz, p.nd, p.L, p.smem_hist != 0, ba.thr != nullptr, p.pairs != 0);
+    // without TMA, rows that start 16-byte aligned are staged with cp.async
+    const bool async = ((size_t)p.W * dsz) % 16 == 0 && ((uintptr_t)field % 16) == 0;
+    const int mode = tma ? MODE_TMA : (async ? MODE_ASYNC : MODE_PLAIN);
     const int items = (int)items64;
     switch (ba.dtype) {
-    case EC_F32:
+    case EC_F32: {
+        const size_t smem = smem_bytes<float>(mode, dsz, p.nd, p.L, p.smem_hist != 0, ba.thr != nullptr, p.pairs != 0);
         if (tma && p.smem_hist && !p.agg) {
             // descriptor sets with compile-time histogram rows
             if (p.pairs) {
-                if (desc == 13u) return launch_t<float, true, false, 13, 3>(map, p, smem, num_sms, items, grid_override, s);
-                if (desc == 15u) return launch_t<float, true, true, 15, 3>(map, p, smem, num_sms, items, grid_override, s);
+                if (desc == 13u) return launch_t<float, MODE_TMA, false, 13, 3>(map, p, smem, num_sms, items, grid_override, s);
+                if (desc == 15u) return launch_t<float, MODE_TMA, true, 15, 3>(map, p, smem, num_sms, items, grid_override, s);
             }
-            if (desc == 1u) return launch_t<float, true, false, 1>(map, p, smem, num_sms, items, grid_override, s);
-            if (desc == 13u) return launch_t<float, true, false, 13>(map, p, smem, num_sms, items, grid_override, s);
-            if (desc == 15u) return launch_t<float, true, true, 15>(map, p, smem, num_sms, items, grid_override, s);
+            if (desc == 1u) return launch_t<float, MODE_TMA, false, 1>(map, p, smem, num_sms, items, grid_override, s);
+            if (desc == 13u) return launch_t<float, MODE_TMA, false, 13>(map, p, smem, num_sms, items, grid_override, s);
+            if (desc == 15u) return launch_t<float, MODE_TMA, true, 15>(map, p, smem, num_sms, items, grid_override, s);
         }
         if (tma && p.agg)
-            return per ? launch_t<float, true, true, 0, 2>(map, p, smem, num_sms, items, grid_override, s)
-                       : launch_t<float, true, false, 0, 2>(map, p, smem, num_sms, items, grid_override, s);
-        if (tma) return per ? launch_t<float, true, true>(map, p, smem, num_sms, items, grid_override, s)
-                            : launch_t<float, true, false>(map, p, smem, num_sms, items, grid_override, s);
-        return per ? launch_t<float, false, true>(map, p, smem, num_sms, items, grid_override, s)
-                   : launch_t<float, false, false>(map, p, smem, num_sms, items, grid_override, s);
-    case EC_U16:
-        return per ? launch_t<uint16_t, false, true>(map, p, smem, num_sms, items, grid_override, s)
-                   : launch_t<uint16_t, false, false>(map, p, smem, num_sms, items, grid_override, s);
-    case EC_U8:
-        return per ? launch_t<uint8_t, false, true>(map, p, smem, num_sms, items, grid_override, s)
-                   : launch_t<uint8_t, false, false>(map, p, smem, num_sms, items, grid_override, s);
+            return per ? launch_t<float, MODE_TMA, true, 0, 2>(map, p, smem, num_sms, items, grid_override, s)
+                       : launch_t<float, MODE_TMA, false, 0, 2>(map, p, smem, num_sms, items, grid_override, s);
+        if (tma) return per ? launch_t<float, MODE_TMA, true>(map, p, smem, num_sms, items, grid_override, s)
+                            : launch_t<float, MODE_TMA, false>(map, p, smem, num_sms, items, grid_override, s);
+        return async ? launch_loads<float, MODE_ASYNC>(map, p, desc, per, smem, num_sms, items, grid_override, s)
+                     : launch_loads<float, MODE_PLAIN>(map, p, desc, per, smem, num_sms, items, grid_override, s);
+    }
+    case EC_U16: {
+        const size_t smem = smem_bytes<uint16_t>(mode, dsz, p.nd, p.L, p.smem_hist != 0, ba.thr != nullptr, false);
+        return async ? launch_loads<uint16_t, MODE_ASYNC>(map, p, desc, per, smem, num_sms, items, grid_override, s)
+                     : launch_loads<uint16_t, MODE_PLAIN>(map, p, desc, per, smem, num_sms, items, grid_override, s);
+    }
+    case EC_U8: {
+        const size_t smem = smem_bytes<uint8_t>(mode, dsz, p.nd, p.L, p.smem_hist != 0, ba.thr != nullptr, false);
+        return async ? launch_loads<uint8_t, MODE_ASYNC>(map, p, desc, per, smem, num_sms, items, grid_override, s)
+                     : launch_loads<uint8_t, MODE_PLAIN>(map, p, desc, per, smem, num_sms, items, grid_override, s);
+    }
     }
     return EC_ERR_DTYPE;
 }

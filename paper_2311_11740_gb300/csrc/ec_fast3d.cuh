@@ -23,6 +23,18 @@ constexpr int NS = 8;                       // float plane ring depth (TMA path)
 constexpr int NK = 4;                       // key plane ring depth
 constexpr int kThrSmem = 4096;
 constexpr int kPairsPerPlane = BY * (BX - 4) / 2;   // key pairs j = 2..69 of 18 rows
+constexpr int KAP = 3;                      // planes copied ahead (asynchronous plain-load path)
+constexpr int NRAWP = KAP + 2;              // raw plane ring: plane being binned, waited, KAP in flight
+
+// Raw plane of the asynchronous path: rows y0-1 .. y0+16, each with the
+// tile's 64 voxels and A elements (16 bytes) of halo on each side, so every
+// 16-byte chunk starts aligned.
+template <typename T>
+constexpr int rpad() { return 16 / (int)sizeof(T); }
+template <typename T>
+constexpr int rrow_bytes() { return (TXF + 2 * rpad<T>()) * (int)sizeof(T); }
+template <typename T>
+constexpr int rplane_bytes() { return BY * rrow_bytes<T>(); }
 
 struct Params {
     const void *field;
@@ -199,6 +211,7 @@ template <typename T>
 struct Ctx {
     Params p;
     float *fring;
+    unsigned char *raw;        // raw plane ring (asynchronous plain-load path)
     uint32_t *kring;
     uint64_t *bars;
     volatile int *abort_flag;
@@ -303,6 +316,59 @@ __device__ __forceinline__ uint32_t bin3_offsets(int tid)
     return (uint32_t)(row * BX + 2 + 2 * jp) | ((uint32_t)(row * KP + jp) << 16);
 }
 static_assert(BY == 18 && (BX - 4) / 2 == 34 && kThreads == 256, "binning shares assume 18 x 34 pairs, 256 threads");
+
+// ---- asynchronous plain-load path: the 18 rows of a plane are copied into
+// shared memory KAP planes ahead with cp.async (16-byte chunks, zero-filled
+// outside the field); used when every row starts 16-byte aligned.
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Start this thread's copies of plane pz (nothing if not wanted) and close
+// them as one group.  Row widths and starts are multiples of 16 bytes, so a
+// chunk lies wholly inside or wholly outside the field.
+template <typename T>
+__device__ __forceinline__ void copy_plane(const Ctx<T> &c, int pz, bool wanted)
+{
+    constexpr int A = rpad<T>(), CPR = rrow_bytes<T>() / 16;
+    if (wanted) {
+        unsigned char *slot = c.raw + (uint32_t)((pz + 16) % NRAWP) * rplane_bytes<T>();
+        const bool zin = pz >= 0 && pz < c.p.D;
+        const T *base = (const T *)c.p.field;
+        for (int q = threadIdx.x; q < BY * CPR; q += kThreads) {
+            const int row = q / CPR, ch = q - row * CPR;
+            const int64_t gy = (int64_t)c.y0 - 1 + row, gx = (int64_t)c.x0 - A + (int64_t)ch * A;
+            const bool in = zin && gy >= 0 && gy < c.p.H && gx >= 0 && gx < c.p.W;
+            cp_async16(smem_u32(slot + row * rrow_bytes<T>() + ch * 16),
+                       in ? base + ((int64_t)pz * c.p.H + gy) * c.p.W + gx : base, in ? 16u : 0u);
+        }
+    }
+    cp_async_commit();
+}
+
+// Bin plane pb from its raw slot into the key ring; values outside the
+// field bin to L.
+template <typename T>
+__device__ __forceinline__ void bin_plane_raw(Ctx<T> &c, int pb, uint32_t *kp)
+{
+    constexpr int A = rpad<T>();
+    const T *raw = (const T *)(c.raw + (uint32_t)((pb + 16) % NRAWP) * rplane_bytes<T>());
+    const uint32_t L = (uint32_t)c.p.L;
+    for (int i = threadIdx.x; i < kPairsPerPlane; i += kThreads) {
+        const int row = i / ((BX - 4) / 2), jp = i - row * ((BX - 4) / 2);
+        const int64_t gy = (int64_t)c.y0 - 1 + row, gx = (int64_t)c.x0 - 2 + 2 * jp;
+        const T *r = raw + row * (rrow_bytes<T>() / (int)sizeof(T)) + A - 2 + 2 * jp;
+        const bool yin = gy >= 0 && gy < c.p.H;
+        const uint32_t b0 = (yin && (c.interior || (gx >= 0 && gx < c.p.W))) ? bin_value(c, r[0]) : L;
+        const uint32_t b1 = (yin && (c.interior || (gx + 1 >= 0 && gx + 1 < c.p.W))) ? bin_value(c, r[1]) : L;
+        kp[row * KP + jp] = b0 | (b1 << 16);
+    }
+}
 
 // Load key plane s+1 into window slot (R+1)%3 and add the contributions of
 // plane s (R = position of plane s in the 3-plane register window).
@@ -522,6 +588,28 @@ __device__ __forceinline__ bool zstep_tma(Ctx<T> &c, const CUtensorMap *tmap, ui
         }
     }
     count_plane<T, PER, R, DM, SCHED>(c, win, h);
+    return true;
+}
+
+// One step of the asynchronous plain-load walk (s = z0 - 3 + t, pb = s + 2):
+// wait for this thread's copies of plane pb, synchronise, bin it, start the
+// copies of plane pb + KAP (into the slot of plane pb - 2, binned two steps
+// ago), then count plane s.  Returns false if the block must stop.
+template <typename T, bool PER, int R, int DM, int SCHED = 0>
+__device__ __forceinline__ bool zstep_async(Ctx<T> &c, uint32_t (&win)[3][3][5], int t)
+{
+    const int s = c.z0 - 3 + t;
+    const int pb = s + 2;
+    cp_async_wait<KAP - 1>();
+    __syncthreads();
+    if (*c.abort_flag) return false;
+    if (pb <= c.z1) {
+        uint32_t *kp = c.kring + (uint32_t)((pb + 8) % NK) * KWORDS;
+        if (pb < c.p.zv0 || pb >= c.p.zv1) fill_never(kp, c.p.L);
+        else bin_plane_raw<T>(c, pb, kp);
+    }
+    copy_plane<T>(c, pb + KAP, pb + KAP <= c.z1);
+    count_plane<T, PER, R, DM, SCHED>(c, win, s);
     return true;
 }
 
