@@ -85,6 +85,40 @@ def test_random_3d(ctx, shape, dtype):
     check(ctx, f, thr, L)
 
 
+# Rows of 16-byte multiples take the cp.async staging (uint8 / uint16, and
+# float32 fields whose storage is not 16-byte aligned take plain loads);
+# partial tiles in x, y and z.
+SHAPES3_ALIGNED = [(3, 17, 80), (9, 33, 144), (66, 5, 48), (1, 1, 16), (2, 19, 208)]
+
+
+@pytest.mark.parametrize("shape", SHAPES3_ALIGNED)
+@pytest.mark.parametrize("dtype", ["u8", "u16"])
+def test_random_3d_aligned_rows(ctx, shape, dtype):
+    rng = np.random.default_rng(zlib.crc32(repr((shape, dtype, "rows")).encode()))
+    smooth = workloads.grf_nd(int(rng.integers(1 << 30)), shape, 2.0).numpy()
+    if dtype == "u8":
+        f, L, thr = workloads.quantize_u8(torch.from_numpy(smooth)).numpy(), 256, None
+    else:
+        f = np.clip(smooth * 300 + 1000, 0, 2000).astype(np.uint16)
+        L, thr = 700, np.sort(rng.integers(0, 2001, size=700)).astype(np.uint16)
+    for desc in (1, 13, 15, 6):
+        check(ctx, f, thr, L, desc=desc, algos=[ec.ALGO_VOXEL])
+
+
+def test_3d_unaligned_float_pointer(ctx):
+    rng = np.random.default_rng(11)
+    shape, L = (7, 20, 64), 90
+    vals = rng.normal(size=shape).astype(np.float32)
+    thr = np.sort(rng.normal(size=L)).astype(np.float32)
+    flat = torch.zeros(vals.size + 1, dtype=torch.float32)
+    flat[1:] = torch.from_numpy(vals.reshape(-1))
+    dev = flat.cuda()[1:].view(shape)
+    assert dev.data_ptr() % 16 != 0
+    got = ec.curve(dev, to_dev(thr), L=L, descriptors=ALL3, ctx=ctx)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(got.cpu().numpy(), oracle.ec_curves(vals, thr, L, 26, ALL3))
+
+
 SHAPES2 = [(1, 1), (1, 9), (7, 1), (3, 5), (17, 255), (16, 256), (15, 257), (64, 300), (65, 513), (200, 3)]
 
 
