@@ -53,6 +53,7 @@ constexpr int kThrMaxB = 4096;
 
 struct Shared {
     uint32_t *kring;
+    unsigned char *raw;    // raw plane ring of the cp.async staging (3D items)
     volatile int *abort_flag;
     int *sh_hist;          // may be too small for a field: then nullptr for that field
     size_t hist_cap;       // ints
@@ -147,6 +148,7 @@ __device__ void item_3d(const BField &F, const BItem &it, const Shared &S, const
     c.p.err = err;
     c.p.agg = 0;
     c.fring = nullptr;
+    c.raw = S.raw;
     c.kring = S.kring;
     c.bars = nullptr;
     c.abort_flag = S.abort_flag;
@@ -168,10 +170,21 @@ __device__ void item_3d(const BField &F, const BItem &it, const Shared &S, const
 #pragma unroll
             for (int e = 0; e < 5; e++) win[a][b][e] = 0;
     const int nsteps = c.z1 - c.z0 + 3;
-    for (int t = 0; t < nsteps; t += 3) {
-        zstep<T, PER, 0, 0>(c, win, t);
-        if (t + 1 < nsteps) zstep<T, PER, 1, 0>(c, win, t + 1);
-        if (t + 2 < nsteps) zstep<T, PER, 2, 0>(c, win, t + 2);
+    if (((uintptr_t)F.field & 3u) == 0) {
+        // planes staged with 4-byte cp.async chunks, KAP planes ahead
+        for (int q = 0; q < KAP; q++) copy_plane<T, 4>(c, c.z0 - 1 + q, c.z0 - 1 + q <= c.z1);
+        for (int t = 0; t < nsteps; t += 3) {
+            zstep_async<T, PER, 0, 0, 0, 4>(c, win, t);
+            if (t + 1 < nsteps) zstep_async<T, PER, 1, 0, 0, 4>(c, win, t + 1);
+            if (t + 2 < nsteps) zstep_async<T, PER, 2, 0, 0, 4>(c, win, t + 2);
+        }
+        cp_async_wait<0>();
+    } else {
+        for (int t = 0; t < nsteps; t += 3) {
+            zstep<T, PER, 0, 0>(c, win, t);
+            if (t + 1 < nsteps) zstep<T, PER, 1, 0>(c, win, t + 1);
+            if (t + 2 < nsteps) zstep<T, PER, 2, 0>(c, win, t + 2);
+        }
     }
 }
 
@@ -256,6 +269,17 @@ __device__ void scan_field(const BField &F)
     }
 }
 
+// Shared memory of k_batch: [key ring] [abort, item broadcast 16] [hist hist_cap ints]
+// [thresholds kThrMaxB words] [raw plane ring (float32 size, 128-byte aligned)].
+__host__ __device__ constexpr size_t batch_raw_offset(size_t hist_cap)
+{
+    return ((size_t)NK * KWORDS * 4 + 16 + hist_cap * 4 + (size_t)kThrMaxB * 4 + 127) / 128 * 128;
+}
+__host__ __device__ constexpr size_t batch_smem_bytes(size_t hist_cap)
+{
+    return batch_raw_offset(hist_cap) + (size_t)NRAWP * rplane4_bytes<float>();
+}
+
 __global__ void __launch_bounds__(kThreads, 2)
 k_batch(const BField *__restrict__ fields, const BItem *__restrict__ items, int nitems, int *counters, int *err,
         size_t hist_cap)
@@ -268,6 +292,7 @@ k_batch(const BField *__restrict__ fields, const BItem *__restrict__ items, int 
     S.sh_hist = (int *)(smem + (size_t)NK * KWORDS * 4 + 16);
     S.hist_cap = hist_cap;
     S.thr = (unsigned char *)(S.sh_hist + hist_cap);
+    S.raw = smem + batch_raw_offset(hist_cap);
     if (threadIdx.x == 0) *S.abort_flag = 0;
     int *next_item = counters;          // counters[0]: item counter; counters[1 + f]: items done per field
     for (;;) {
@@ -467,7 +492,7 @@ extern "C" int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, voi
 
     // ---- launch configuration
     const size_t hist_cap = std::max<size_t>(max_smem_entries, 1);
-    const size_t smem = (size_t)NK * KWORDS * 4 + 16 + hist_cap * 4 + (size_t)kThrMaxB * 4;
+    const size_t smem = batch_smem_bytes(hist_cap);
     EC_CUDA(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kThreads, smem));
