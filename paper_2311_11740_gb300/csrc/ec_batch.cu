@@ -170,13 +170,13 @@ __device__ void item_3d(const BField &F, const BItem &it, const Shared &S, const
 #pragma unroll
             for (int e = 0; e < 5; e++) win[a][b][e] = 0;
     const int nsteps = c.z1 - c.z0 + 3;
-    if (((uintptr_t)F.field & 3u) == 0) {
-        // planes staged with 4-byte cp.async chunks, KAP planes ahead
-        for (int q = 0; q < KAP; q++) copy_plane<T, 4>(c, c.z0 - 1 + q, c.z0 - 1 + q <= c.z1);
+    if (((uintptr_t)F.field & 15u) == 0) {
+        // planes staged with 16-byte cp.async chunks covering each row, KAP planes ahead
+        for (int q = 0; q < KAP; q++) copy_plane<T, STG_COVER>(c, c.z0 - 1 + q, c.z0 - 1 + q <= c.z1);
         for (int t = 0; t < nsteps; t += 3) {
-            zstep_async<T, PER, 0, 0, 0, 4>(c, win, t);
-            if (t + 1 < nsteps) zstep_async<T, PER, 1, 0, 0, 4>(c, win, t + 1);
-            if (t + 2 < nsteps) zstep_async<T, PER, 2, 0, 0, 4>(c, win, t + 2);
+            zstep_async<T, PER, 0, 0, 0, STG_COVER>(c, win, t);
+            if (t + 1 < nsteps) zstep_async<T, PER, 1, 0, 0, STG_COVER>(c, win, t + 1);
+            if (t + 2 < nsteps) zstep_async<T, PER, 2, 0, 0, STG_COVER>(c, win, t + 2);
         }
         cp_async_wait<0>();
     } else {
@@ -277,7 +277,7 @@ __host__ __device__ constexpr size_t batch_raw_offset(size_t hist_cap)
 }
 __host__ __device__ constexpr size_t batch_smem_bytes(size_t hist_cap)
 {
-    return batch_raw_offset(hist_cap) + (size_t)NRAWP * rplane4_bytes<float>();
+    return batch_raw_offset(hist_cap) + (size_t)NRAWP * rplane_bytes<float>();
 }
 
 __global__ void __launch_bounds__(kThreads, 2)

@@ -60,17 +60,17 @@ __global__ void k_uniform_check(const float *t, int L, int *uni)
 #endif
 
 // Staging modes of the fast 3D kernel.
-// MODE_ASYNC: cp.async 16-byte chunks (rows start 16-byte aligned);
-// MODE_ASYNC4: cp.async 4-byte chunks (any width, field 4-byte aligned).
-enum { MODE_PLAIN = 0, MODE_TMA = 1, MODE_ASYNC = 2, MODE_ASYNC4 = 3 };
+// MODE_ASYNC: cp.async 16-byte chunks, rows start 16-byte aligned;
+// MODE_COVER: cp.async 16-byte chunks covering rows of any width (field
+// start 16-byte aligned).
+enum { MODE_PLAIN = 0, MODE_TMA = 1, MODE_ASYNC = 2, MODE_COVER = 3 };
 
 template <typename T>
 constexpr size_t stage_bytes(int mode)
 {
     return mode == MODE_TMA      ? (size_t)NS * FSTRIDE * sizeof(float)
-           : mode == MODE_ASYNC  ? ((size_t)NRAWP * rplane_bytes<T>() + 127) / 128 * 128
-           : mode == MODE_ASYNC4 ? ((size_t)NRAWP * rplane4_bytes<T>() + 127) / 128 * 128
-                                 : 0;
+           : (mode == MODE_ASYNC || mode == MODE_COVER) ? ((size_t)NRAWP * rplane_bytes<T>() + 127) / 128 * 128
+                                                         : 0;
 }
 
 template <typename T, int MODE, bool PER, int DM, int SCHED = 0>
@@ -204,15 +204,15 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
                 if (t + 1 < nsteps && !zstep_tma<T, PER, 1, DM, SCHED>(c, &tmap, win, t + 1)) return;
                 if (t + 2 < nsteps && !zstep_tma<T, PER, 2, DM, SCHED>(c, &tmap, win, t + 2)) return;
             }
-        } else if constexpr (MODE == MODE_ASYNC || MODE == MODE_ASYNC4) {
-            constexpr int CH = MODE == MODE_ASYNC ? 16 : 4;
-            for (int q = 0; q < KAP; q++) copy_plane<T, CH>(c, c.z0 - 1 + q, c.z0 - 1 + q <= c.z1);
+        } else if constexpr (MODE == MODE_ASYNC || MODE == MODE_COVER) {
+            constexpr int STG = MODE == MODE_ASYNC ? STG_ALIGNED : STG_COVER;
+            for (int q = 0; q < KAP; q++) copy_plane<T, STG>(c, c.z0 - 1 + q, c.z0 - 1 + q <= c.z1);
             const int nsteps = c.z1 - c.z0 + 3;
             bool ok = true;
             for (int t = 0; ok && t < nsteps; t += 3) {
-                ok = zstep_async<T, PER, 0, DM, SCHED, CH>(c, win, t);
-                if (ok && t + 1 < nsteps) ok = zstep_async<T, PER, 1, DM, SCHED, CH>(c, win, t + 1);
-                if (ok && t + 2 < nsteps) ok = zstep_async<T, PER, 2, DM, SCHED, CH>(c, win, t + 2);
+                ok = zstep_async<T, PER, 0, DM, SCHED, STG>(c, win, t);
+                if (ok && t + 1 < nsteps) ok = zstep_async<T, PER, 1, DM, SCHED, STG>(c, win, t + 1);
+                if (ok && t + 2 < nsteps) ok = zstep_async<T, PER, 2, DM, SCHED, STG>(c, win, t + 2);
             }
             cp_async_wait<0>();
             if (!ok) return;
@@ -321,7 +321,7 @@ template <typename T, int MODE>
 static int launch_loads(const CUtensorMap &map, const Params &p, uint32_t desc, bool per, size_t smem, int num_sms,
                         int items, int grid_override, cudaStream_t s)
 {
-    if constexpr (MODE == MODE_ASYNC || MODE == MODE_ASYNC4) {
+    if constexpr (MODE == MODE_ASYNC || MODE == MODE_COVER) {
         if (p.smem_hist) {
             if (desc == 1u) return launch_t<T, MODE, false, 1>(map, p, smem, num_sms, items, grid_override, s);
             if (desc == 13u) return launch_t<T, MODE, false, 13>(map, p, smem, num_sms, items, grid_override, s);
@@ -396,11 +396,12 @@ int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, 
         }
     }
     if (ha.schedule == 3 && ha.smem_hist && tma && (desc == 13u || desc == 15u)) p.pairs = 1;
-    // without TMA, rows are staged with cp.async: 16-byte chunks when every
-    // row starts 16-byte aligned, else 4-byte chunks (field 4-byte aligned)
-    const bool async = ((size_t)p.W * dsz) % 16 == 0 && ((uintptr_t)field % 16) == 0;
-    const bool async4 = ((uintptr_t)field % 4) == 0;
-    const int mode = tma ? MODE_TMA : (async ? MODE_ASYNC : (async4 ? MODE_ASYNC4 : MODE_PLAIN));
+    // without TMA, rows are staged with 16-byte cp.async chunks when the field
+    // starts 16-byte aligned: whole rows if every row does too, else the
+    // aligned cover of each row
+    const bool cover = ((uintptr_t)field % 16) == 0;
+    const bool async = cover && ((size_t)p.W * dsz) % 16 == 0;
+    const int mode = tma ? MODE_TMA : (async ? MODE_ASYNC : (cover ? MODE_COVER : MODE_PLAIN));
     const int items = (int)items64;
     switch (ba.dtype) {
     case EC_F32: {
@@ -421,19 +422,19 @@ int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, 
         if (tma) return per ? launch_t<float, MODE_TMA, true>(map, p, smem, num_sms, items, grid_override, s)
                             : launch_t<float, MODE_TMA, false>(map, p, smem, num_sms, items, grid_override, s);
         if (async) return launch_loads<float, MODE_ASYNC>(map, p, desc, per, smem, num_sms, items, grid_override, s);
-        if (async4) return launch_loads<float, MODE_ASYNC4>(map, p, desc, per, smem, num_sms, items, grid_override, s);
+        if (cover) return launch_loads<float, MODE_COVER>(map, p, desc, per, smem, num_sms, items, grid_override, s);
         return launch_loads<float, MODE_PLAIN>(map, p, desc, per, smem, num_sms, items, grid_override, s);
     }
     case EC_U16: {
         const size_t smem = smem_bytes<uint16_t>(mode, dsz, p.nd, p.L, p.smem_hist != 0, ba.thr != nullptr, false);
         if (async) return launch_loads<uint16_t, MODE_ASYNC>(map, p, desc, per, smem, num_sms, items, grid_override, s);
-        if (async4) return launch_loads<uint16_t, MODE_ASYNC4>(map, p, desc, per, smem, num_sms, items, grid_override, s);
+        if (cover) return launch_loads<uint16_t, MODE_COVER>(map, p, desc, per, smem, num_sms, items, grid_override, s);
         return launch_loads<uint16_t, MODE_PLAIN>(map, p, desc, per, smem, num_sms, items, grid_override, s);
     }
     case EC_U8: {
         const size_t smem = smem_bytes<uint8_t>(mode, dsz, p.nd, p.L, p.smem_hist != 0, ba.thr != nullptr, false);
         if (async) return launch_loads<uint8_t, MODE_ASYNC>(map, p, desc, per, smem, num_sms, items, grid_override, s);
-        if (async4) return launch_loads<uint8_t, MODE_ASYNC4>(map, p, desc, per, smem, num_sms, items, grid_override, s);
+        if (cover) return launch_loads<uint8_t, MODE_COVER>(map, p, desc, per, smem, num_sms, items, grid_override, s);
         return launch_loads<uint8_t, MODE_PLAIN>(map, p, desc, per, smem, num_sms, items, grid_override, s);
     }
     }

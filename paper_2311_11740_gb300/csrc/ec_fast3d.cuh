@@ -35,12 +35,12 @@ template <typename T>
 constexpr int rrow_bytes() { return (TXF + 2 * rpad<T>()) * (int)sizeof(T); }
 template <typename T>
 constexpr int rplane_bytes() { return BY * rrow_bytes<T>(); }
-// 4-byte-chunk staging (rows of any width): a row slot holds the 4-byte
-// aligned cover of the row's in-field part of x0-2 .. x0+65.
-template <typename T>
-constexpr int rrow4_bytes() { return (68 * (int)sizeof(T) + 8 + 15) / 16 * 16; }
-template <typename T>
-constexpr int rplane4_bytes() { return BY * rrow4_bytes<T>(); }
+// Staging kinds of the cp.async path: STG_ALIGNED, rows start 16-byte
+// aligned and a row slot holds x0-A .. x0+63+A; STG_COVER, rows of any
+// width (field start 16-byte aligned) and a row slot holds the 16-byte
+// aligned cover of the row's in-field part of x0-2 .. x0+65 (at most
+// 68 * sizeof(T) + 15 bytes: the same slot size).
+enum { STG_ALIGNED = 0, STG_COVER = 1 };
 
 struct Params {
     const void *field;
@@ -331,28 +331,24 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src, uint32_t src_bytes)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Start this thread's copies of plane pz (nothing if not wanted) and close
-// them as one group.  CH = 16: row widths and starts are multiples of 16
-// bytes, so a chunk lies wholly inside or wholly outside the field.  CH = 4
-// (any width; field pointer 4-byte aligned): each row copies the 4-byte
-// aligned cover of its in-field part, the last chunk of the field clipped to
-// the field's end; a warp takes a row, its lanes the row's chunks.
-template <typename T, int CH>
+// them as one group.  STG_ALIGNED: row widths and starts are multiples of 16
+// bytes, so a chunk lies wholly inside or wholly outside the field.
+// STG_COVER: each row copies the 16-byte aligned cover of its in-field part
+// (bytes of neighbouring rows in the cover are never read), the field's last
+// chunk clipped to its end.
+template <typename T, int STG>
 __device__ __forceinline__ void copy_plane(const Ctx<T> &c, int pz, bool wanted)
 {
+    constexpr int A = rpad<T>(), CPR = rrow_bytes<T>() / 16, sz = (int)sizeof(T);
     if (wanted) {
         const bool zin = pz >= 0 && pz < c.p.D;
-        if constexpr (CH == 16) {
-            constexpr int A = rpad<T>(), CPR = rrow_bytes<T>() / 16;
-            unsigned char *slot = c.raw + (uint32_t)((pz + 16) % NRAWP) * rplane_bytes<T>();
+        unsigned char *slot = c.raw + (uint32_t)((pz + 16) % NRAWP) * rplane_bytes<T>();
+        if constexpr (STG == STG_ALIGNED) {
             const T *base = (const T *)c.p.field;
             for (int q = threadIdx.x; q < BY * CPR; q += kThreads) {
                 const int row = q / CPR, ch = q - row * CPR;
@@ -361,25 +357,19 @@ __device__ __forceinline__ void copy_plane(const Ctx<T> &c, int pz, bool wanted)
                 cp_async16(smem_u32(slot + row * rrow_bytes<T>() + ch * 16),
                            in ? base + ((int64_t)pz * c.p.H + gy) * c.p.W + gx : base, in ? 16u : 0u);
             }
-        } else {
-            constexpr int sz = (int)sizeof(T);
-            unsigned char *slot = c.raw + (uint32_t)((pz + 16) % NRAWP) * rplane4_bytes<T>();
+        } else if (zin) {
             const unsigned char *fb = (const unsigned char *)c.p.field;
             const int64_t total = c.p.D * c.p.H * c.p.W * sz;
             const int64_t xlo = max((int64_t)c.x0 - 2, (int64_t)0), xhi = min((int64_t)c.x0 + 66, c.p.W);
-            const int lane = threadIdx.x & 31;
-            if (zin) {
-                for (int row = threadIdx.x >> 5; row < BY; row += kThreads / 32) {
-                    const int64_t gy = (int64_t)c.y0 - 1 + row;
-                    if (gy < 0 || gy >= c.p.H) continue;
-                    const int64_t r0 = ((int64_t)pz * c.p.H + gy) * c.p.W;
-                    const int64_t a = ((r0 + xlo) * sz) & ~(int64_t)3, e = (r0 + xhi) * sz;
-                    const uint32_t dst = smem_u32(slot + row * rrow4_bytes<T>());
-                    for (int64_t cs = a + 4 * lane; cs < e; cs += 128) {
-                        const int64_t left = total - cs;
-                        cp_async4(dst + (uint32_t)(cs - a), fb + cs, left < 4 ? (uint32_t)left : 4u);
-                    }
-                }
+            for (int q = threadIdx.x; q < BY * CPR; q += kThreads) {
+                const int row = q / CPR, ch = q - row * CPR;
+                const int64_t gy = (int64_t)c.y0 - 1 + row;
+                if (gy < 0 || gy >= c.p.H) continue;
+                const int64_t rs = (((int64_t)pz * c.p.H + gy) * c.p.W + xlo) * sz;
+                const int64_t cs = (rs & ~(int64_t)15) + 16 * ch;
+                if (cs >= rs + (xhi - xlo) * sz) continue;
+                const int64_t left = total - cs;
+                cp_async16(smem_u32(slot + row * rrow_bytes<T>() + ch * 16), fb + cs, left < 16 ? (uint32_t)left : 16u);
             }
         }
     }
@@ -388,39 +378,29 @@ __device__ __forceinline__ void copy_plane(const Ctx<T> &c, int pz, bool wanted)
 
 // Bin plane pb from its raw slot into the key ring; values outside the
 // field bin to L.
-template <typename T, int CH>
+template <typename T, int STG>
 __device__ __forceinline__ void bin_plane_raw(Ctx<T> &c, int pb, uint32_t *kp)
 {
-    constexpr int sz = (int)sizeof(T);
+    constexpr int A = rpad<T>(), sz = (int)sizeof(T);
     const uint32_t L = (uint32_t)c.p.L;
-    if constexpr (CH == 16) {
-        constexpr int A = rpad<T>();
-        const T *raw = (const T *)(c.raw + (uint32_t)((pb + 16) % NRAWP) * rplane_bytes<T>());
-        for (int i = threadIdx.x; i < kPairsPerPlane; i += kThreads) {
-            const int row = i / ((BX - 4) / 2), jp = i - row * ((BX - 4) / 2);
-            const int64_t gy = (int64_t)c.y0 - 1 + row, gx = (int64_t)c.x0 - 2 + 2 * jp;
-            const T *r = raw + row * (rrow_bytes<T>() / sz) + A - 2 + 2 * jp;
-            const bool yin = gy >= 0 && gy < c.p.H;
-            const uint32_t b0 = (yin && (c.interior || (gx >= 0 && gx < c.p.W))) ? bin_value(c, r[0]) : L;
-            const uint32_t b1 = (yin && (c.interior || (gx + 1 >= 0 && gx + 1 < c.p.W))) ? bin_value(c, r[1]) : L;
-            kp[row * KP + jp] = b0 | (b1 << 16);
+    const unsigned char *raw = c.raw + (uint32_t)((pb + 16) % NRAWP) * rplane_bytes<T>();
+    const int64_t xlo = max((int64_t)c.x0 - 2, (int64_t)0);
+    for (int i = threadIdx.x; i < kPairsPerPlane; i += kThreads) {
+        const int row = i / ((BX - 4) / 2), jp = i - row * ((BX - 4) / 2);
+        const int64_t gy = (int64_t)c.y0 - 1 + row, gx = (int64_t)c.x0 - 2 + 2 * jp;
+        const bool yin = gy >= 0 && gy < c.p.H;
+        const unsigned char *r;
+        if constexpr (STG == STG_ALIGNED) {
+            r = raw + row * rrow_bytes<T>() + (A - 2 + 2 * jp) * sz;
+        } else {
+            // the slot starts at the 16-byte boundary below element xlo of the row
+            const int off = (int)(((((int64_t)pb * c.p.H + gy) * c.p.W + xlo) * sz) & 15);
+            r = raw + row * rrow_bytes<T>() + off + (gx - xlo) * sz;
         }
-    } else {
-        const unsigned char *raw = c.raw + (uint32_t)((pb + 16) % NRAWP) * rplane4_bytes<T>();
-        const int64_t xlo = max((int64_t)c.x0 - 2, (int64_t)0);
-        for (int i = threadIdx.x; i < kPairsPerPlane; i += kThreads) {
-            const int row = i / ((BX - 4) / 2), jp = i - row * ((BX - 4) / 2);
-            const int64_t gy = (int64_t)c.y0 - 1 + row, gx = (int64_t)c.x0 - 2 + 2 * jp;
-            const bool yin = gy >= 0 && gy < c.p.H;
-            // byte of element x in the row slot: the slot starts at the 4-byte
-            // boundary below element xlo of the row
-            const int off = (int)((((int64_t)pb * c.p.H + gy) * c.p.W + xlo) * sz & 3);
-            const unsigned char *r = raw + row * rrow4_bytes<T>() + off;
-            uint32_t b0 = L, b1 = L;
-            if (yin && gx >= 0 && gx < c.p.W) b0 = bin_value(c, *(const T *)(r + (gx - xlo) * sz));
-            if (yin && gx + 1 >= 0 && gx + 1 < c.p.W) b1 = bin_value(c, *(const T *)(r + (gx + 1 - xlo) * sz));
-            kp[row * KP + jp] = b0 | (b1 << 16);
-        }
+        const uint32_t b0 = (yin && (c.interior || (gx >= 0 && gx < c.p.W))) ? bin_value(c, *(const T *)r) : L;
+        const uint32_t b1 =
+            (yin && (c.interior || (gx + 1 >= 0 && gx + 1 < c.p.W))) ? bin_value(c, *(const T *)(r + sz)) : L;
+        kp[row * KP + jp] = b0 | (b1 << 16);
     }
 }
 
@@ -649,7 +629,7 @@ __device__ __forceinline__ bool zstep_tma(Ctx<T> &c, const CUtensorMap *tmap, ui
 // wait for this thread's copies of plane pb, synchronise, bin it, start the
 // copies of plane pb + KAP (into the slot of plane pb - 2, binned two steps
 // ago), then count plane s.  Returns false if the block must stop.
-template <typename T, bool PER, int R, int DM, int SCHED = 0, int CH = 16>
+template <typename T, bool PER, int R, int DM, int SCHED = 0, int STG = STG_ALIGNED>
 __device__ __forceinline__ bool zstep_async(Ctx<T> &c, uint32_t (&win)[3][3][5], int t)
 {
     const int s = c.z0 - 3 + t;
@@ -660,9 +640,9 @@ __device__ __forceinline__ bool zstep_async(Ctx<T> &c, uint32_t (&win)[3][3][5],
     if (pb <= c.z1) {
         uint32_t *kp = c.kring + (uint32_t)((pb + 8) % NK) * KWORDS;
         if (pb < c.p.zv0 || pb >= c.p.zv1) fill_never(kp, c.p.L);
-        else bin_plane_raw<T, CH>(c, pb, kp);
+        else bin_plane_raw<T, STG>(c, pb, kp);
     }
-    copy_plane<T, CH>(c, pb + KAP, pb + KAP <= c.z1);
+    copy_plane<T, STG>(c, pb + KAP, pb + KAP <= c.z1);
     count_plane<T, PER, R, DM, SCHED>(c, win, s);
     return true;
 }
