@@ -129,7 +129,7 @@ __device__ IBin<T> make_ibin(const BField &F, const Shared &S)
     return ib;
 }
 
-template <typename T, bool PER>
+template <typename T, bool PER, int DM = 0>
 __device__ void item_3d(const BField &F, const BItem &it, const Shared &S, const FBin &fb, int *err)
 {
     Ctx<T> c;
@@ -174,16 +174,16 @@ __device__ void item_3d(const BField &F, const BItem &it, const Shared &S, const
         // planes staged with 16-byte cp.async chunks covering each row, KAP planes ahead
         for (int q = 0; q < KAP; q++) copy_plane<T, STG_COVER>(c, c.z0 - 1 + q, c.z0 - 1 + q <= c.z1);
         for (int t = 0; t < nsteps; t += 3) {
-            zstep_async<T, PER, 0, 0, 0, STG_COVER>(c, win, t);
-            if (t + 1 < nsteps) zstep_async<T, PER, 1, 0, 0, STG_COVER>(c, win, t + 1);
-            if (t + 2 < nsteps) zstep_async<T, PER, 2, 0, 0, STG_COVER>(c, win, t + 2);
+            zstep_async<T, PER, 0, DM, 0, STG_COVER>(c, win, t);
+            if (t + 1 < nsteps) zstep_async<T, PER, 1, DM, 0, STG_COVER>(c, win, t + 1);
+            if (t + 2 < nsteps) zstep_async<T, PER, 2, DM, 0, STG_COVER>(c, win, t + 2);
         }
         cp_async_wait<0>();
     } else {
         for (int t = 0; t < nsteps; t += 3) {
-            zstep<T, PER, 0, 0>(c, win, t);
-            if (t + 1 < nsteps) zstep<T, PER, 1, 0>(c, win, t + 1);
-            if (t + 2 < nsteps) zstep<T, PER, 2, 0>(c, win, t + 2);
+            zstep<T, PER, 0, DM>(c, win, t);
+            if (t + 1 < nsteps) zstep<T, PER, 1, DM>(c, win, t + 1);
+            if (t + 2 < nsteps) zstep<T, PER, 2, DM>(c, win, t + 2);
         }
     }
 }
@@ -271,6 +271,15 @@ __device__ void scan_field(const BField &F)
 
 // Shared memory of k_batch: [key ring] [abort, item broadcast 16] [hist hist_cap ints]
 // [thresholds kThrMaxB words] [raw plane ring (float32 size, 128-byte aligned)].
+// Compile-time descriptor rows of a field (0: none), as in the single-field kernel.
+__device__ __forceinline__ int batch_dm(const BField &F)
+{
+    uint32_t desc = 0;
+    for (int i = 0; i < kMaxDesc; i++)
+        if (F.rows[i] >= 0) desc |= 1u << i;
+    return (desc == 1u || desc == 13u || desc == 15u) ? (int)desc : 0;
+}
+
 __host__ __device__ constexpr size_t batch_raw_offset(size_t hist_cap)
 {
     return ((size_t)NK * KWORDS * 4 + 16 + hist_cap * 4 + (size_t)kThrMaxB * 4 + 127) / 128 * 128;
@@ -294,6 +303,8 @@ k_batch(const BField *__restrict__ fields, const BItem *__restrict__ items, int 
     S.thr = (unsigned char *)(S.sh_hist + hist_cap);
     S.raw = smem + batch_raw_offset(hist_cap);
     if (threadIdx.x == 0) *S.abort_flag = 0;
+    int loaded_f = -1;   // field whose binning tables are in shared memory
+    FBin fb{};
     int *next_item = counters;          // counters[0]: item counter; counters[1 + f]: items done per field
     for (;;) {
         __syncthreads();
@@ -303,14 +314,27 @@ k_batch(const BField *__restrict__ fields, const BItem *__restrict__ items, int 
         if (i >= nitems) break;
         const BItem it = items[i];
         const BField F = fields[it.f];
+        // float32 3D items with the common descriptor sets use compile-time
+        // rows: their shared histogram is interleaved per level, [L+1][nd]
+        const int dm = (F.ndim == 3 && F.dtype == EC_F32 && F.smem_hist) ? batch_dm(F) : 0;
+        const int hn = dm ? F.nd * (F.L + 1) : F.nd * F.L;
         if (F.smem_hist)
-            for (int k = threadIdx.x; k < F.nd * F.L; k += blockDim.x) S.sh_hist[k] = 0;
-        FBin fb{};
-        load_binning(F, S, fb);   // ends with a barrier
+            for (int k = threadIdx.x; k < hn; k += blockDim.x) S.sh_hist[k] = 0;
+        if (it.f != loaded_f) {
+            load_binning(F, S, fb);   // ends with a barrier
+            loaded_f = it.f;
+        } else {
+            __syncthreads();
+        }
         if (F.ndim == 3) {
             const bool per = F.rows[1] >= 0;
             switch (F.dtype) {
-            case EC_F32: per ? item_3d<float, true>(F, it, S, fb, err) : item_3d<float, false>(F, it, S, fb, err); break;
+            case EC_F32:
+                if (dm == 15) item_3d<float, true, 15>(F, it, S, fb, err);
+                else if (dm == 13) item_3d<float, false, 13>(F, it, S, fb, err);
+                else if (dm == 1) item_3d<float, false, 1>(F, it, S, fb, err);
+                else per ? item_3d<float, true>(F, it, S, fb, err) : item_3d<float, false>(F, it, S, fb, err);
+                break;
             case EC_U16: per ? item_3d<uint16_t, true>(F, it, S, fb, err) : item_3d<uint16_t, false>(F, it, S, fb, err); break;
             default: per ? item_3d<uint8_t, true>(F, it, S, fb, err) : item_3d<uint8_t, false>(F, it, S, fb, err); break;
             }
@@ -332,7 +356,13 @@ k_batch(const BField *__restrict__ fields, const BItem *__restrict__ items, int 
         __syncthreads();
         if (F.smem_hist)
             for (int k = threadIdx.x; k < F.nd * F.L; k += blockDim.x) {
-                const int v = S.sh_hist[k];
+                int v;
+                if (dm) {
+                    const int r = k / F.L, lv = k - r * F.L;
+                    v = S.sh_hist[lv * F.nd + r];
+                } else {
+                    v = S.sh_hist[k];
+                }
                 if (v) atomicAdd((unsigned long long *)&F.hist[k], (unsigned long long)(long long)v);
             }
         __threadfence();
@@ -416,7 +446,7 @@ extern "C" int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, voi
         F.nd = rm.nd;
         for (int k = 0; k < kMaxDesc; k++) F.rows[k] = rm.row[k];
         F.smem_hist = use_smem_hist(rm.nd, d.L) ? 1 : 0;
-        if (F.smem_hist) max_smem_entries = std::max(max_smem_entries, (size_t)rm.nd * d.L);
+        if (F.smem_hist) max_smem_entries = std::max(max_smem_entries, (size_t)rm.nd * ((size_t)d.L + 1));
         F.hist = (long long *)(uintptr_t)hist_entries;   // offset, fixed up below
         hist_entries += (size_t)rm.nd * d.L;
         F.done_idx = (int)bf.size();
