@@ -225,7 +225,12 @@ __device__ void item_2d(const BField &F, const BItem &it, const Shared &S, const
     for (int a = 0; a < 3; a++)
 #pragma unroll
         for (int e = 0; e < 5; e++) win[a][e] = 0;
-    fast2d::walk_item_2d<T, CONN4, 0>(c, win);
+    if (((uintptr_t)F.field & 15u) == 0) {
+        c.raw = S.raw;   // rows staged with 16-byte cp.async covers, three rows ahead
+        fast2d::walk_item_2d_async<T, CONN4, 0, STG_COVER>(c, win);
+    } else {
+        fast2d::walk_item_2d<T, CONN4, 0>(c, win);
+    }
 }
 
 // Running sums of one field's histogram into its output (one block).

@@ -26,7 +26,11 @@ namespace ec {
 
 namespace fast2d {
 
-template <typename T, bool CONN4, int DM, bool ASYNC>
+// Row staging of the 2D kernel: per-pixel loads one row ahead, or cp.async
+// rows three rows ahead (whole 16-byte aligned rows, or 16-byte covers).
+enum { ROWS_LOADS = 0, ROWS_ALIGNED = 1, ROWS_COVER = 2 };
+
+template <typename T, bool CONN4, int DM, int ROWS>
 __global__ void __launch_bounds__(kThreads, 3) k_pixel2d_fast(Params p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -36,7 +40,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_pixel2d_fast(Params p)
     c.ring = (uint32_t *)smem;
     unsigned char *tail = smem + (size_t)NR * RWORDS * 4;
     c.raw = tail;
-    if (ASYNC) tail += (size_t)NRAW * raw_bytes<T>();
+    if (ROWS != ROWS_LOADS) tail += (size_t)NRAW * raw_bytes<T>();
     const int L = p.L;
     c.sh_hist = nullptr;
     if (p.smem_hist) {
@@ -110,7 +114,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_pixel2d_fast(Params p)
         c.y1 = (int)min((int64_t)c.y0 + p.ry, p.H);
         c.interior = c.x0 >= 2 && c.x0 + SW + 2 <= p.W;
         __syncthreads();   // ring reuse across items
-        if constexpr (ASYNC) walk_item_2d_async<T, CONN4, DM>(c, win);
+        if constexpr (ROWS == ROWS_ALIGNED) walk_item_2d_async<T, CONN4, DM, fast3d::STG_ALIGNED>(c, win);
+        else if constexpr (ROWS == ROWS_COVER) walk_item_2d_async<T, CONN4, DM, fast3d::STG_COVER>(c, win);
         else walk_item_2d<T, CONN4, DM>(c, win);
     }
     if (c.sh_hist) {
@@ -130,11 +135,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_pixel2d_fast(Params p)
 }
 
 template <typename T, bool CONN4, int DM = 0>
-static int launch_t(const Params &p, size_t smem, int num_sms, int items, int grid_override, bool async,
+static int launch_t(const Params &p, size_t smem, int num_sms, int items, int grid_override, int rows,
                     cudaStream_t s)
 {
-    auto kern = async ? k_pixel2d_fast<T, CONN4, DM, true> : k_pixel2d_fast<T, CONN4, DM, false>;
-    if (async) smem += (size_t)NRAW * raw_bytes<T>();
+    auto kern = rows == ROWS_ALIGNED ? k_pixel2d_fast<T, CONN4, DM, ROWS_ALIGNED>
+                : rows == ROWS_COVER ? k_pixel2d_fast<T, CONN4, DM, ROWS_COVER>
+                                     : k_pixel2d_fast<T, CONN4, DM, ROWS_LOADS>;
+    if (rows != ROWS_LOADS) smem += (size_t)NRAW * raw_bytes<T>();
     EC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
@@ -146,17 +153,16 @@ static int launch_t(const Params &p, size_t smem, int num_sms, int items, int gr
     return EC_OK;
 }
 
-// async: every row starts 16-byte aligned, so rows can be copied with cp.async
 template <typename T>
-static int launch_dt(const Params &p, uint32_t desc, size_t smem, int num_sms, int items, int grid, bool async,
+static int launch_dt(const Params &p, uint32_t desc, size_t smem, int num_sms, int items, int grid, int rows,
                      cudaStream_t s)
 {
     if (p.smem_hist && !p.conn4) {
-        if (desc == 1u) return launch_t<T, false, 1>(p, smem, num_sms, items, grid, async, s);
-        if (desc == 7u) return launch_t<T, false, 7>(p, smem, num_sms, items, grid, async, s);
+        if (desc == 1u) return launch_t<T, false, 1>(p, smem, num_sms, items, grid, rows, s);
+        if (desc == 7u) return launch_t<T, false, 7>(p, smem, num_sms, items, grid, rows, s);
     }
-    return p.conn4 ? launch_t<T, true>(p, smem, num_sms, items, grid, async, s)
-                   : launch_t<T, false>(p, smem, num_sms, items, grid, async, s);
+    return p.conn4 ? launch_t<T, true>(p, smem, num_sms, items, grid, rows, s)
+                   : launch_t<T, false>(p, smem, num_sms, items, grid, rows, s);
 }
 
 }  // namespace fast2d
@@ -204,11 +210,14 @@ int launch_fast_2d(const void *field, const int64_t dims[2], const BinArgs &ba, 
     if (dsz == 1) smem += 512;
     else if (ba.thr && p.L <= kThrSmem) smem += ((size_t)p.L * dsz + 15) & ~(size_t)15;
     const int items = (int)items64;
-    const bool async = ((size_t)p.W * dsz) % 16 == 0 && ((uintptr_t)field % 16) == 0;
+    // rows copied with cp.async when the field starts 16-byte aligned: whole
+    // rows if every row starts aligned too, else their 16-byte covers
+    const bool cover = ((uintptr_t)field % 16) == 0;
+    const int rows = !cover ? ROWS_LOADS : (((size_t)p.W * dsz) % 16 == 0 ? ROWS_ALIGNED : ROWS_COVER);
     switch (ba.dtype) {
-    case EC_F32: return launch_dt<float>(p, desc, smem, num_sms, items, grid_override, async, s);
-    case EC_U16: return launch_dt<uint16_t>(p, desc, smem, num_sms, items, grid_override, async, s);
-    case EC_U8: return launch_dt<uint8_t>(p, desc, smem, num_sms, items, grid_override, async, s);
+    case EC_F32: return launch_dt<float>(p, desc, smem, num_sms, items, grid_override, rows, s);
+    case EC_U16: return launch_dt<uint16_t>(p, desc, smem, num_sms, items, grid_override, rows, s);
+    case EC_U8: return launch_dt<uint8_t>(p, desc, smem, num_sms, items, grid_override, rows, s);
     }
     return EC_ERR_DTYPE;
 }

@@ -198,20 +198,35 @@ using fast3d::cp_async_commit;
 using fast3d::cp_async_wait;
 
 // Start this thread's copies of row y (empty if y is beyond the item) and
-// close them as one group.  The row width and start are multiples of 16
-// bytes, so a chunk lies wholly inside or wholly outside the field.
-template <typename T>
+// close them as one group.  STG_ALIGNED: the row width and start are
+// multiples of 16 bytes, so a chunk lies wholly inside or wholly outside the
+// field.  STG_COVER (rows of any width, field start 16-byte aligned): the
+// 16-byte aligned cover of the row's in-field part of x0-2 .. x0+SW+1, the
+// field's last chunk clipped to its end.
+template <typename T, int STG>
 __device__ __forceinline__ void copy_row(const Ctx2<T> &c, int64_t y, bool wanted)
 {
-    constexpr int A = raw_pad<T>(), NCH = raw_bytes<T>() / 16;
-    if (wanted) {
+    constexpr int A = raw_pad<T>(), NCH = raw_bytes<T>() / 16, sz = (int)sizeof(T);
+    if (wanted && y >= 0 && y < c.p.H) {
         unsigned char *slot = c.raw + (uint32_t)((y + 16) % NRAW) * raw_bytes<T>();
-        const bool yin = y >= 0 && y < c.p.H;
-        const T *base = (const T *)c.p.field;
-        for (int q = threadIdx.x; q < NCH; q += kThreads) {
-            const int64_t x = (int64_t)c.x0 - A + (int64_t)q * A;
-            const bool in = yin && x >= 0 && x < c.p.W;
-            cp_async16(fast3d::smem_u32(slot + q * 16), in ? base + y * c.p.W + x : base, in ? 16u : 0u);
+        if constexpr (STG == fast3d::STG_ALIGNED) {
+            const T *base = (const T *)c.p.field;
+            for (int q = threadIdx.x; q < NCH; q += kThreads) {
+                const int64_t x = (int64_t)c.x0 - A + (int64_t)q * A;
+                const bool in = x >= 0 && x < c.p.W;
+                cp_async16(fast3d::smem_u32(slot + q * 16), in ? base + y * c.p.W + x : base, in ? 16u : 0u);
+            }
+        } else {
+            const unsigned char *fb = (const unsigned char *)c.p.field;
+            const int64_t total = c.p.H * c.p.W * sz;
+            const int64_t xlo = max((int64_t)c.x0 - 2, (int64_t)0), xhi = min((int64_t)c.x0 + SW + 2, c.p.W);
+            const int64_t rs = (y * c.p.W + xlo) * sz, re = (y * c.p.W + xhi) * sz;
+            for (int q = threadIdx.x; q < NCH; q += kThreads) {
+                const int64_t cs = (rs & ~(int64_t)15) + 16 * q;
+                if (cs >= re) break;
+                const int64_t left = total - cs;
+                cp_async16(fast3d::smem_u32(slot + q * 16), fb + cs, left < 16 ? (uint32_t)left : 16u);
+            }
         }
     }
     cp_async_commit();
@@ -219,22 +234,28 @@ __device__ __forceinline__ void copy_row(const Ctx2<T> &c, int64_t y, bool wante
 
 // Bin row y from its raw slot into ring slot (y mod NR); pixels outside the
 // field bin to L.
-template <typename T>
+template <typename T, int STG>
 __device__ __forceinline__ void bin_row_raw(Ctx2<T> &c, int64_t y)
 {
-    constexpr int A = raw_pad<T>();
+    constexpr int A = raw_pad<T>(), sz = (int)sizeof(T);
     uint32_t *kr = c.ring + (uint32_t)((y + 8) % NR) * RWORDS;
-    const T *raw = (const T *)(c.raw + (uint32_t)((y + 16) % NRAW) * raw_bytes<T>());
+    const unsigned char *raw = c.raw + (uint32_t)((y + 16) % NRAW) * raw_bytes<T>();
     const uint32_t L = (uint32_t)c.p.L;
     const bool yin = y >= 0 && y < c.p.H;
+    const int64_t xlo = max((int64_t)c.x0 - 2, (int64_t)0);
+    // byte of pixel x0-2 in the slot (may lie before the slot for the first strip: never read then)
+    int64_t b0x;
+    if constexpr (STG == fast3d::STG_ALIGNED) b0x = (int64_t)(A - 2) * sz;
+    else b0x = (((y * c.p.W + xlo) * sz) & 15) - (xlo - ((int64_t)c.x0 - 2)) * sz;
 #pragma unroll
     for (int it = 0; it < (RWORDS + kThreads - 1) / kThreads; it++) {
         const int w = threadIdx.x + it * kThreads;
         if (w < RWORDS) {
             const int64_t gx = (int64_t)c.x0 - 2 + 2 * w;
-            const int ri = 2 * w - 2 + A;
-            const uint32_t b0 = (yin && (c.interior || (gx >= 0 && gx < c.p.W))) ? bin_value2(c, raw[ri]) : L;
-            const uint32_t b1 = (yin && (c.interior || (gx + 1 >= 0 && gx + 1 < c.p.W))) ? bin_value2(c, raw[ri + 1]) : L;
+            const unsigned char *r = raw + b0x + 2 * w * sz;
+            const uint32_t b0 = (yin && (c.interior || (gx >= 0 && gx < c.p.W))) ? bin_value2(c, *(const T *)r) : L;
+            const uint32_t b1 =
+                (yin && (c.interior || (gx + 1 >= 0 && gx + 1 < c.p.W))) ? bin_value2(c, *(const T *)(r + sz)) : L;
             kr[w] = b0 | (b1 << 16);
         }
     }
@@ -243,12 +264,12 @@ __device__ __forceinline__ void bin_row_raw(Ctx2<T> &c, int64_t y)
 // Asynchronous row step, y = y0 - 2 + t: bin row y+1 (its copies finished
 // before the previous barrier), start the copies of row y+2+KA, wait for
 // this thread's copies of row y+2, synchronise, then count as ystep does.
-template <typename T, bool CONN4, int R, int DM>
+template <typename T, bool CONN4, int R, int DM, int STG>
 __device__ __forceinline__ void ystep_async(Ctx2<T> &c, uint32_t (&win)[3][5], int t)
 {
     const int y = c.y0 - 2 + t;
-    bin_row_raw<T>(c, y + 1);
-    copy_row<T>(c, y + 2 + KA, y + 2 + KA <= c.y1);
+    bin_row_raw<T, STG>(c, y + 1);
+    copy_row<T, STG>(c, y + 2 + KA, y + 2 + KA <= c.y1);
     cp_async_wait<KA>();
     __syncthreads();
     count_row<T, CONN4, R, DM>(c, win, y);
@@ -269,17 +290,17 @@ __device__ __forceinline__ void walk_item_2d(Ctx2<T> &c, uint32_t (&win)[3][5])
 }
 
 // Asynchronous walk of one item (same rows as walk_item_2d).
-template <typename T, bool CONN4, int DM>
+template <typename T, bool CONN4, int DM, int STG>
 __device__ __forceinline__ void walk_item_2d_async(Ctx2<T> &c, uint32_t (&win)[3][5])
 {
-    for (int q = 0; q <= KA; q++) copy_row<T>(c, c.y0 - 1 + q, c.y0 - 1 + q <= c.y1);
+    for (int q = 0; q <= KA; q++) copy_row<T, STG>(c, c.y0 - 1 + q, c.y0 - 1 + q <= c.y1);
     cp_async_wait<KA>();
     __syncthreads();
     const int nsteps = c.y1 - c.y0 + 2;
     for (int t = 0; t < nsteps; t += 3) {
-        ystep_async<T, CONN4, 0, DM>(c, win, t);
-        if (t + 1 < nsteps) ystep_async<T, CONN4, 1, DM>(c, win, t + 1);
-        if (t + 2 < nsteps) ystep_async<T, CONN4, 2, DM>(c, win, t + 2);
+        ystep_async<T, CONN4, 0, DM, STG>(c, win, t);
+        if (t + 1 < nsteps) ystep_async<T, CONN4, 1, DM, STG>(c, win, t + 1);
+        if (t + 2 < nsteps) ystep_async<T, CONN4, 2, DM, STG>(c, win, t + 2);
     }
     cp_async_wait<0>();
 }
