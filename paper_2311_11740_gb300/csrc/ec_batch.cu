@@ -172,7 +172,7 @@ __device__ void item_3d(const BField &F, const BItem &it, const Shared &S, const
     const int nsteps = c.z1 - c.z0 + 3;
     if (((uintptr_t)F.field & 15u) == 0) {
         // planes staged with 16-byte cp.async chunks covering each row, KAP planes ahead
-        for (int q = 0; q < KAP; q++) copy_plane<T, STG_COVER>(c, c.z0 - 1 + q, c.z0 - 1 + q <= c.z1);
+        for (int q = 0; q < KAP; q++) copy_plane<T, STG_COVER, NRAWP>(c, c.z0 - 1 + q, c.z0 - 1 + q <= c.z1);
         for (int t = 0; t < nsteps; t += 3) {
             zstep_async<T, PER, 0, DM, 0, STG_COVER>(c, win, t);
             if (t + 1 < nsteps) zstep_async<T, PER, 1, DM, 0, STG_COVER>(c, win, t + 1);

@@ -69,7 +69,7 @@ template <typename T>
 constexpr size_t stage_bytes(int mode)
 {
     return mode == MODE_TMA      ? (size_t)NS * FSTRIDE * sizeof(float)
-           : (mode == MODE_ASYNC || mode == MODE_COVER) ? ((size_t)NRAWP * rplane_bytes<T>() + 127) / 128 * 128
+           : (mode == MODE_ASYNC || mode == MODE_COVER) ? ((size_t)NRAWP2 * rplane_bytes<T>() + 127) / 128 * 128
                                                          : 0;
 }
 
@@ -206,16 +206,7 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
             }
         } else if constexpr (MODE == MODE_ASYNC || MODE == MODE_COVER) {
             constexpr int STG = MODE == MODE_ASYNC ? STG_ALIGNED : STG_COVER;
-            for (int q = 0; q < KAP; q++) copy_plane<T, STG>(c, c.z0 - 1 + q, c.z0 - 1 + q <= c.z1);
-            const int nsteps = c.z1 - c.z0 + 3;
-            bool ok = true;
-            for (int t = 0; ok && t < nsteps; t += 3) {
-                ok = zstep_async<T, PER, 0, DM, SCHED, STG>(c, win, t);
-                if (ok && t + 1 < nsteps) ok = zstep_async<T, PER, 1, DM, SCHED, STG>(c, win, t + 1);
-                if (ok && t + 2 < nsteps) ok = zstep_async<T, PER, 2, DM, SCHED, STG>(c, win, t + 2);
-            }
-            cp_async_wait<0>();
-            if (!ok) return;
+            if (!walk_item_async2<T, PER, DM, SCHED, STG>(c, win)) return;
         } else {
             const int nsteps = c.z1 - c.z0 + 3;
             for (int t = 0; t < nsteps; t += 3) {

@@ -23,8 +23,9 @@ constexpr int NS = 8;                       // float plane ring depth (TMA path)
 constexpr int NK = 4;                       // key plane ring depth
 constexpr int kThrSmem = 4096;
 constexpr int kPairsPerPlane = BY * (BX - 4) / 2;   // key pairs j = 2..69 of 18 rows
-constexpr int KAP = 3;                      // planes copied ahead (asynchronous plain-load path)
-constexpr int NRAWP = KAP + 2;              // raw plane ring: plane being binned, waited, KAP in flight
+constexpr int KAP = 3;                      // planes copied ahead by the one-plane cp.async walk (ec_batch)
+constexpr int NRAWP = KAP + 2;              // its raw plane ring: plane being binned, waited, KAP in flight
+constexpr int NRAWP2 = 6;                   // raw plane ring of the two-plane cp.async walk: 2 binned, 4 in flight
 
 // Raw plane of the asynchronous path: rows y0-1 .. y0+16, each with the
 // tile's 64 voxels and A elements (16 bytes) of halo on each side, so every
@@ -341,13 +342,13 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // STG_COVER: each row copies the 16-byte aligned cover of its in-field part
 // (bytes of neighbouring rows in the cover are never read), the field's last
 // chunk clipped to its end.
-template <typename T, int STG>
+template <typename T, int STG, int NRING = NRAWP2, bool COMMIT = true>
 __device__ __forceinline__ void copy_plane(const Ctx<T> &c, int pz, bool wanted)
 {
     constexpr int A = rpad<T>(), CPR = rrow_bytes<T>() / 16, sz = (int)sizeof(T);
     if (wanted) {
         const bool zin = pz >= 0 && pz < c.p.D;
-        unsigned char *slot = c.raw + (uint32_t)((pz + 16) % NRAWP) * rplane_bytes<T>();
+        unsigned char *slot = c.raw + (uint32_t)((pz + 16) % NRING) * rplane_bytes<T>();
         if constexpr (STG == STG_ALIGNED) {
             const T *base = (const T *)c.p.field;
             for (int q = threadIdx.x; q < BY * CPR; q += kThreads) {
@@ -373,7 +374,42 @@ __device__ __forceinline__ void copy_plane(const Ctx<T> &c, int pz, bool wanted)
             }
         }
     }
-    cp_async_commit();
+    if (COMMIT) cp_async_commit();
+}
+
+// One value pair (row, jp) of a raw plane slot into the key plane.
+template <typename T, int STG>
+__device__ __forceinline__ void bin_pair_raw(Ctx<T> &c, uint32_t *kp, const unsigned char *raw, int pb, int row, int jp)
+{
+    constexpr int A = rpad<T>(), sz = (int)sizeof(T);
+    const uint32_t L = (uint32_t)c.p.L;
+    const int64_t gy = (int64_t)c.y0 - 1 + row, gx = (int64_t)c.x0 - 2 + 2 * jp;
+    const bool yin = gy >= 0 && gy < c.p.H;
+    const unsigned char *r;
+    if constexpr (STG == STG_ALIGNED) {
+        r = raw + row * rrow_bytes<T>() + (A - 2 + 2 * jp) * sz;
+    } else {
+        const int64_t xlo = max((int64_t)c.x0 - 2, (int64_t)0);
+        const int off = (int)(((((int64_t)pb * c.p.H + gy) * c.p.W + xlo) * sz) & 15);
+        r = raw + row * rrow_bytes<T>() + off + (gx - xlo) * sz;
+    }
+    const uint32_t b0 = (yin && (c.interior || (gx >= 0 && gx < c.p.W))) ? bin_value(c, *(const T *)r) : L;
+    const uint32_t b1 = (yin && (c.interior || (gx + 1 >= 0 && gx + 1 < c.p.W))) ? bin_value(c, *(const T *)(r + sz)) : L;
+    kp[row * KP + jp] = b0 | (b1 << 16);
+}
+
+// Bin a raw plane with the fixed per-thread shares of bin_plane_f32 (pairs
+// tc and tc+16 of row tr, plus the leftover pair of bin3 when `extra`).
+template <typename T, int STG>
+__device__ __forceinline__ void bin_plane_raw2(Ctx<T> &c, int pb, uint32_t *kp, bool extra)
+{
+    const unsigned char *raw = c.raw + (uint32_t)((pb + 16) % NRAWP2) * rplane_bytes<T>();
+    bin_pair_raw<T, STG>(c, kp, raw, pb, c.tr, c.tc);
+    bin_pair_raw<T, STG>(c, kp, raw, pb, c.tr, c.tc + 16);
+    if (extra && c.bin3 != ~0u) {
+        const int ko = (int)(c.bin3 >> 16), row = ko / KP;
+        bin_pair_raw<T, STG>(c, kp, raw, pb, row, ko - row * KP);
+    }
 }
 
 // Bin plane pb from its raw slot into the key ring; values outside the
@@ -625,7 +661,9 @@ __device__ __forceinline__ bool zstep_tma(Ctx<T> &c, const CUtensorMap *tmap, ui
     return true;
 }
 
-// One step of the asynchronous plain-load walk (s = z0 - 3 + t, pb = s + 2):
+// One step of the one-plane cp.async walk (s = z0 - 3 + t, pb = s + 2),
+// used by the batched kernel, whose register budget the two-plane walk
+// exceeds:
 // wait for this thread's copies of plane pb, synchronise, bin it, start the
 // copies of plane pb + KAP (into the slot of plane pb - 2, binned two steps
 // ago), then count plane s.  Returns false if the block must stop.
@@ -642,9 +680,60 @@ __device__ __forceinline__ bool zstep_async(Ctx<T> &c, uint32_t (&win)[3][3][5],
         if (pb < c.p.zv0 || pb >= c.p.zv1) fill_never(kp, c.p.L);
         else bin_plane_raw<T, STG>(c, pb, kp);
     }
-    copy_plane<T, STG>(c, pb + KAP, pb + KAP <= c.z1);
+    copy_plane<T, STG, NRAWP>(c, pb + KAP, pb + KAP <= c.z1);
     count_plane<T, PER, R, DM, SCHED>(c, win, s);
     return true;
+}
+
+// One half-step of the two-plane cp.async walk (same plane schedule as
+// zstep_tma), counting plane h = z0 - 4 + t.  Barrier steps (t even): wait
+// for this thread's copies of planes h+3 and h+4 (issued two barrier steps
+// ago), synchronise, bin them, and start the copies of planes h+7 and h+8
+// (one group) into the slots of planes h+1 and h+2, binned one barrier step
+// ago.  Returns false if the block must stop.
+template <typename T, bool PER, int R, int DM, int SCHED, int STG>
+__device__ __forceinline__ bool zstep_async2(Ctx<T> &c, uint32_t (&win)[3][3][5], int t)
+{
+    const int h = c.z0 - 4 + t;
+    if ((t & 1) == 0) {
+        cp_async_wait<1>();
+        __syncthreads();
+        if (*c.abort_flag) return false;
+#pragma unroll
+        for (int q = 3; q <= 4; q++) {
+            const int pb = h + q;
+            if (pb > c.z1) break;
+            uint32_t *kp = c.kring + (uint32_t)((pb + 8) % NK) * KWORDS;
+            if (pb < c.p.zv0 || pb >= c.p.zv1) fill_never(kp, c.p.L);
+            else bin_plane_raw2<T, STG>(c, pb, kp, (q == 3) == (threadIdx.x < 128));
+        }
+        copy_plane<T, STG, NRAWP2, false>(c, h + 7, h + 7 <= c.z1);
+        copy_plane<T, STG, NRAWP2, false>(c, h + 8, h + 8 <= c.z1);
+        cp_async_commit();
+    }
+    count_plane<T, PER, R, DM, SCHED>(c, win, h);
+    return true;
+}
+
+// Walk one item with zstep_async2: planes z0-1 .. z1 binned, z0 .. z1-1 counted.
+template <typename T, bool PER, int DM, int SCHED, int STG>
+__device__ __forceinline__ bool walk_item_async2(Ctx<T> &c, uint32_t (&win)[3][3][5])
+{
+    copy_plane<T, STG, NRAWP2, false>(c, c.z0 - 1, true);
+    copy_plane<T, STG, NRAWP2, false>(c, c.z0, c.z0 <= c.z1);
+    cp_async_commit();
+    copy_plane<T, STG, NRAWP2, false>(c, c.z0 + 1, c.z0 + 1 <= c.z1);
+    copy_plane<T, STG, NRAWP2, false>(c, c.z0 + 2, c.z0 + 2 <= c.z1);
+    cp_async_commit();
+    const int nsteps = c.z1 - c.z0 + 4;
+    bool ok = true;
+    for (int t = 0; ok && t < nsteps; t += 3) {
+        ok = zstep_async2<T, PER, 0, DM, SCHED, STG>(c, win, t);
+        if (ok && t + 1 < nsteps) ok = zstep_async2<T, PER, 1, DM, SCHED, STG>(c, win, t + 1);
+        if (ok && t + 2 < nsteps) ok = zstep_async2<T, PER, 2, DM, SCHED, STG>(c, win, t + 2);
+    }
+    cp_async_wait<0>();
+    return ok;
 }
 
 }  // namespace fast3d
