@@ -105,13 +105,6 @@ int ec::validate_request(int ndim, const void *field, const int64_t *dims, int d
 
 namespace {
 
-int64_t numel(int ndim, const int64_t *dims)
-{
-    int64_t n = 1;
-    for (int i = 0; i < ndim; i++) n *= dims[i];
-    return n;
-}
-
 int run_curve(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int dtype, const void *thr,
               int32_t L, int connectivity, uint32_t descriptors, int64_t *out, cudaStream_t s)
 {

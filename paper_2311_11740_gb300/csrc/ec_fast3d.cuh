@@ -505,7 +505,6 @@ __device__ __forceinline__ void count_plane(Ctx<T> &c, uint32_t (&win)[3][3][5],
                         }
                     }
                 }
-                return;
             } else {
                 // interleaved rows [L+1][ND]: one address per voxel, the rows at
                 // immediate offsets; the never-active level L has its own
@@ -519,10 +518,8 @@ __device__ __forceinline__ void count_plane(Ctx<T> &c, uint32_t (&win)[3][3][5],
                     if (DM & 4) atomicAdd(e + dm_row<DM, 2>(), arv[v]);
                     if (DM & 8) atomicAdd(e + dm_row<DM, 3>(), 1);
                 }
-                return;
             }
-        }
-        if constexpr (SCHED == 2) {
+        } else if constexpr (SCHED == 2) {
             // warp-aggregated update with descriptor rows known at run time
             const uint32_t lane = threadIdx.x & 31u;
 #pragma unroll
@@ -546,20 +543,20 @@ __device__ __forceinline__ void count_plane(Ctx<T> &c, uint32_t (&win)[3][3][5],
                     }
                 }
             }
-            return;
-        }
+        } else {
 #pragma unroll
-        for (int v = 0; v < 4; v++) {
-            const uint32_t k = key[v];
-            if (k >= (uint32_t)L) continue;
-            const int vals[4] = {ecv[v], pev[v], arv[v], 1};
+            for (int v = 0; v < 4; v++) {
+                const uint32_t k = key[v];
+                if (k >= (uint32_t)L) continue;
+                const int vals[4] = {ecv[v], pev[v], arv[v], 1};
 #pragma unroll
-            for (int dsc = 0; dsc < kMaxDesc; dsc++) {
-                const int r = c.p.rows[dsc];
-                if (r < 0 || vals[dsc] == 0) continue;
-                if (c.sh_hist) atomicAdd(&c.sh_hist[r * L + k], vals[dsc]);
-                else atomicAdd((unsigned long long *)&c.p.hist[(size_t)r * L + k],
-                               (unsigned long long)(long long)vals[dsc]);
+                for (int dsc = 0; dsc < kMaxDesc; dsc++) {
+                    const int r = c.p.rows[dsc];
+                    if (r < 0 || vals[dsc] == 0) continue;
+                    if (c.sh_hist) atomicAdd(&c.sh_hist[r * L + k], vals[dsc]);
+                    else atomicAdd((unsigned long long *)&c.p.hist[(size_t)r * L + k],
+                                   (unsigned long long)(long long)vals[dsc]);
+                }
             }
         }
     }
