@@ -130,7 +130,12 @@ int ec_curve_2d(ec_ctx *ctx, const void *field_dev, const int64_t dims[2], int d
 
 /* EC / perimeter / area / volume curves of a 3D field resident on the device.
  * Same conventions; dims = {d, h, w}.  Algorithm 3 of the paper (Appendix),
- * Table 2 weights, 26-connectivity. */
+ * Table 2 weights, 26-connectivity.
+ * Performance note (results do not depend on it): float32 fields whose start
+ * is 16-byte aligned and whose row length is a multiple of 4 are staged by
+ * the tensor memory accelerator; other fields that start 16-byte aligned by
+ * asynchronous 16-byte copies; fields that start unaligned by plain loads
+ * (slowest).  The same holds for ec_curve_2d's rows. */
 int ec_curve_3d(ec_ctx *ctx, const void *field_dev, const int64_t dims[3], int dtype,
                 const void *thresholds_dev, int32_t L, int connectivity,
                 uint32_t descriptors, int64_t *out_dev, void *stream);
