@@ -188,22 +188,24 @@ def batched_vs_per_field(ec, ctx, n_requests, seed=5):
                                            ctx=ctx, out=o) for d, o in zip(fields, outs)], 3)
     bat_ms = time_device(lambda: ec.batch(fields, ctx=ctx), 5)
     same = all(torch.equal(a, b) for a, b in zip(outs, ec.batch(fields, ctx=ctx)))
-    # served: page-locked host fields; first a closed-loop pass (everything
-    # submitted at once) gives the server's capacity, then Poisson arrivals at
-    # 0.9 of that capacity give the latency distribution
+    # served: page-locked host fields, one long-lived server warmed by one
+    # untimed burst; a closed-loop pass (the whole burst submitted at once)
+    # gives the server's capacity, then Poisson arrivals at 0.9 of that
+    # capacity give the latency distribution
     host = [(d["field"].cpu().pin_memory(), None if d["thresholds"] is None else d["thresholds"].cpu().numpy(),
              d["L"], d["descriptors"]) for d in fields]
     want = [o.cpu().numpy() for o in outs]
     sv = ec.Server(device_mem_budget=8 << 30, max_slots=8, ctx=ctx)
+    served_ok = all(np.array_equal(sv.wait(t, 600000), w) for t, w in zip(sv.submit_many(host), want))
     t0 = time.perf_counter()
-    tickets = [sv.submit(f, thr, L=Lr, descriptors=dsc) for f, thr, Lr, dsc in host]
-    served_ok = all(np.array_equal(sv.wait(t, 600000), w) for t, w in zip(tickets, want))
+    tickets = sv.submit_many(host)   # the whole burst in one call
+    sv.wait_all(600000)
     cap_s = time.perf_counter() - t0
-    sv.close()
+    served_ok &= all(np.array_equal(sv.result(t), w) for t, w in zip(tickets, want))
     rate = 0.9 * len(host) / cap_s
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, size=len(host))
-    sv = ec.Server(device_mem_budget=8 << 30, max_slots=8, ctx=ctx)
+    sv.reset_stats()
     t0 = time.perf_counter()
     due = t0
     tickets = []

@@ -221,16 +221,25 @@ size_t ec_workspace_bytes(int dtype, int32_t ndim, const int64_t *dims, int32_t 
 
 /* ------------------------------------------------------------------ serving
  * A request loop that admits fields while earlier ones are on the GPU
- * (continuous batching): a request is admitted when a slot is free and its
- * device bytes fit in `device_mem_budget`; admitted requests are copied and
- * computed on their own streams, so their work overlaps on the device.
- * Request fields, thresholds and outputs are host pointers that must stay
- * valid until the request is done.                                         */
+ * (continuous batching): when one of `max_slots` slots is free, the run of
+ * queued requests at the head of the queue whose device bytes fit in
+ * `device_mem_budget` (at most 256 requests and 64 MiB of fields, or one
+ * larger request) is admitted as a group; a group's inputs are copied in,
+ * its curves computed by one batched launch (ec_batch) on the slot's own
+ * stream and context, and its outputs copied back, so groups overlap on the
+ * device.  Under light load a group is a single request.  Request fields,
+ * thresholds and outputs are host pointers that must stay valid until the
+ * request is done.                                                         */
 typedef struct ec_server ec_server;
 int ec_server_create(ec_ctx *ctx, size_t device_mem_budget, int32_t max_slots, ec_server **server);
 /* Queue a request; *ticket identifies it.  EC_ERR_BUSY if the pending queue
  * is full; EC_ERR_OOM if the request alone exceeds the budget. */
 int ec_server_submit(ec_server *server, const ec_field_desc *request, uint64_t *ticket);
+/* Queue n requests in order under one lock (a burst from a front end):
+ * tickets[i] identifies request i.  All are validated first; if one is
+ * malformed (EC_ERR_ARG), exceeds the budget alone (EC_ERR_OOM) or the queue
+ * has no room for all (EC_ERR_BUSY), none is queued. */
+int ec_server_submit_many(ec_server *server, const ec_field_desc *requests, int32_t n, uint64_t *tickets);
 /* *done = 1 once the request finished; *status is its ec_status. */
 int ec_server_poll(ec_server *server, uint64_t ticket, int *done, int32_t *status);
 /* Block until the request is done or timeout_ms passes (EC_ERR_TIMEOUT). */
@@ -239,6 +248,11 @@ int ec_server_wait(ec_server *server, uint64_t ticket, int64_t timeout_ms, int32
  * out[0] = count, out[1] = p50 us, out[2] = p99 us, out[3] = mean us,
  * out[4] = first-submit-to-last-completion us. */
 int ec_server_stats(ec_server *server, double out[5]);
+/* Block until every request submitted so far is done, or timeout_ms passes
+ * (EC_ERR_TIMEOUT). */
+int ec_server_wait_all(ec_server *server, int64_t timeout_ms);
+/* Forget the statistics of requests finished so far (e.g. after a warm-up). */
+int ec_server_reset_stats(ec_server *server);
 int ec_server_destroy(ec_server *server);
 
 /* ---------------------------------------------------- host-side inspection

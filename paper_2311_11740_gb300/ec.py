@@ -71,6 +71,9 @@ def lib():
             L.ec_selfcheck_rules.restype = I64
             L.ec_server_create.argtypes = [P, ctypes.c_size_t, I32, ctypes.POINTER(P)]
             L.ec_server_submit.argtypes = [P, ctypes.POINTER(FieldDesc), ctypes.POINTER(ctypes.c_uint64)]
+            L.ec_server_submit_many.argtypes = [P, ctypes.POINTER(FieldDesc), I32, ctypes.POINTER(ctypes.c_uint64)]
+            L.ec_server_reset_stats.argtypes = [P]
+            L.ec_server_wait_all.argtypes = [P, I64]
             L.ec_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int32)]
             L.ec_server_wait.argtypes = [P, ctypes.c_uint64, I64, ctypes.POINTER(ctypes.c_int32)]
@@ -270,9 +273,7 @@ class Server:
         self.handle = h
         self._keep = {}
 
-    def submit(self, field, thresholds=None, L=None, connectivity=None, descriptors=EC_DESC_EC):
-        """field: host numpy array or CPU torch tensor (page-locked memory
-        overlaps the copies); thresholds: host array of the field's dtype."""
+    def _prepare(self, field, thresholds, L, connectivity, descriptors):
         if hasattr(field, "data_ptr"):
             field = field.contiguous()
         if thresholds is not None:
@@ -281,11 +282,35 @@ class Server:
             thresholds = np.ascontiguousarray(thresholds, dtype=_NP_DTYPES[dtype_code(field)])
             L = thresholds.size if L is None else L
         out = np.zeros((n_rows(descriptors), L), dtype=np.int64)
-        d = _desc(field, thresholds, L, connectivity, descriptors, out)
+        return _desc(field, thresholds, L, connectivity, descriptors, out), (field, thresholds, out)
+
+    def submit(self, field, thresholds=None, L=None, connectivity=None, descriptors=EC_DESC_EC):
+        """field: host numpy array or CPU torch tensor (page-locked memory
+        overlaps the copies); thresholds: host array of the field's dtype."""
+        d, keep = self._prepare(field, thresholds, L, connectivity, descriptors)
         t = ctypes.c_uint64()
         _check(lib().ec_server_submit(self.handle, ctypes.byref(d), ctypes.byref(t)))
-        self._keep[t.value] = (field, thresholds, out)
+        self._keep[t.value] = keep
         return t.value
+
+    def submit_many(self, requests):
+        """Queue a burst of requests, each (field, thresholds, L, descriptors)
+        or a dict of submit()'s arguments, in order under one lock; returns the
+        tickets.  All or none are queued."""
+        descs, keeps = [], []
+        for r in requests:
+            kw = r if isinstance(r, dict) else dict(zip(("field", "thresholds", "L", "descriptors"), r))
+            d, keep = self._prepare(kw["field"], kw.get("thresholds"), kw.get("L"), kw.get("connectivity"),
+                                    kw.get("descriptors", EC_DESC_EC))
+            descs.append(d)
+            keeps.append(keep)
+        n = len(descs)
+        arr = (FieldDesc * n)(*descs)
+        tickets = (ctypes.c_uint64 * n)()
+        _check(lib().ec_server_submit_many(self.handle, arr, n, tickets))
+        for t, keep in zip(tickets, keeps):
+            self._keep[t] = keep
+        return list(tickets)
 
     def poll(self, ticket):
         done, st = ctypes.c_int(), ctypes.c_int32()
@@ -301,6 +326,13 @@ class Server:
 
     def result(self, ticket):
         return self._keep[ticket][2]
+
+    def wait_all(self, timeout_ms: int = 600000):
+        """Block until every request submitted so far is done."""
+        _check(lib().ec_server_wait_all(self.handle, int(timeout_ms)))
+
+    def reset_stats(self):
+        _check(lib().ec_server_reset_stats(self.handle))
 
     def stats(self):
         out = (ctypes.c_double * 5)()

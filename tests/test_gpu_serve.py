@@ -57,6 +57,25 @@ def test_served_pinned_torch_fields(ctx):
     sv.close()
 
 
+def test_submit_many_is_all_or_none(ctx):
+    reqs = _requests(20, seed=11)
+    sv = ec.Server(device_mem_budget=256 << 20, max_slots=3, ctx=ctx)
+    tickets = sv.submit_many(reqs)
+    assert len(tickets) == len(reqs) and len(set(tickets)) == len(reqs)
+    sv.wait_all(120000)
+    for t, (f, thr, L, d) in zip(tickets, reqs):
+        assert sv.poll(t) == (True, 0)
+        np.testing.assert_array_equal(sv.result(t), oracle.ec_curves(f, thr, L, 8 if f.ndim == 2 else 26, d))
+    # one malformed request rejects the whole burst, naming its index
+    bad = list(reqs[:3]) + [dict(field=reqs[0][0], thresholds=reqs[0][1], L=reqs[0][2], descriptors=7,
+                                 connectivity=5)]
+    with pytest.raises(ec.ECError) as e:
+        sv.submit_many(bad)
+    assert e.value.status == 1 and "request 3" in str(e.value)
+    assert sv.stats()["count"] == len(reqs)
+    sv.close()
+
+
 def test_admission_budget_slots_and_failures(ctx):
     big = workloads.config3(n=160, nblobs=50, L=300)
     f, thr = big[0].numpy(), big[1].numpy()
