@@ -46,13 +46,17 @@ LAUNCHES_PER_STEP = 3   # spacing check, histogram kernel, scan
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_voxel3d_fast_512cube_f32.json")
 
 
+# Files that define the profiled kernel (k_voxel3d_fast and what it inlines):
+# the stored ncu traffic is used only while they are unchanged.
+KERNEL_SOURCES = ("ec_fast3d.cu", "ec_fast3d.cuh", "ec_swar.h", "ec_rules.h", "ec_internal.h")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2311_11740_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".h", ".cuh")) and f.startswith("ec_"):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
