@@ -46,7 +46,7 @@ struct BField {
 
 struct BItem {
     int f;
-    int x0, y0, z0, z1;   // 2D: z0..z1 are the item's rows
+    int x0, y0, z0, z1;   // 2D: z0..z1 are the item's rows; y0 > 1: that many row bands (banded strip)
 };
 
 constexpr int kThrMaxB = 4096;
@@ -220,6 +220,14 @@ __device__ void item_2d(const BField &F, const BItem &it, const Shared &S, const
     c.y0 = it.z0;
     c.y1 = it.z1;
     c.interior = c.x0 >= 2 && c.x0 + fast2d::SW + 2 <= c.p.W;
+    if (it.y0 > 1) {
+        // banded strip: virtual rows 0 .. min(kBandRows, rows) of nb bands
+        c.nb = it.y0;
+        c.yb0 = it.z0;
+        c.y0 = 0;
+        c.y1 = min(fast2d::kBandRows, it.z1 - it.z0);
+        c.interior = false;
+    }
     uint32_t win[3][5];
 #pragma unroll
     for (int a = 0; a < 3; a++)
@@ -227,7 +235,8 @@ __device__ void item_2d(const BField &F, const BItem &it, const Shared &S, const
         for (int e = 0; e < 5; e++) win[a][e] = 0;
     if (((uintptr_t)F.field & 15u) == 0) {
         c.raw = S.raw;   // rows staged with 16-byte cp.async covers, three rows ahead
-        fast2d::walk_item_2d_async<T, CONN4, 0, STG_COVER>(c, win);
+        if (c.nb > 1) fast2d::walk_item_2d_async<T, CONN4, 0, STG_COVER, true>(c, win);
+        else fast2d::walk_item_2d_async<T, CONN4, 0, STG_COVER, false>(c, win);
     } else {
         fast2d::walk_item_2d<T, CONN4, 0>(c, win);
     }
@@ -467,11 +476,34 @@ extern "C" int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, voi
                     }
         } else {
             F.dims[0] = 1; F.dims[1] = d.dims[0]; F.dims[2] = d.dims[1];
-            for (int64_t y = 0; y < d.dims[0]; y += 64)
-                for (int64_t x = 0; x < d.dims[1]; x += fast2d::SW) {
-                    items.push_back(BItem{f, (int)x, 0, (int)y, (int)std::min<int64_t>(y + 64, d.dims[0])});
+            // narrow fields (cover staging) share a strip between 2 or 4 row bands
+            int nb = 1;
+            if (((uintptr_t)d.field & 15u) == 0) {
+                const int w4 = d.dtype == EC_F32 ? fast2d::band_max_width<float>(4)
+                               : d.dtype == EC_U16 ? fast2d::band_max_width<uint16_t>(4)
+                                                   : fast2d::band_max_width<uint8_t>(4);
+                const int w2 = d.dtype == EC_F32 ? fast2d::band_max_width<float>(2)
+                               : d.dtype == EC_U16 ? fast2d::band_max_width<uint16_t>(2)
+                                                   : fast2d::band_max_width<uint8_t>(2);
+                // 1, 2 or 4 bands (segments of 1024, 512 or 256 pixels); a band
+                // past the field's last row is all invalid pixels
+                const int64_t bands = (d.dims[0] + fast2d::kBandRows - 1) / fast2d::kBandRows;
+                if (d.dims[1] <= w4 && bands >= 3) nb = 4;
+                else if (d.dims[1] <= w2 && bands >= 2) nb = 2;
+            }
+            if (nb > 1) {
+                const int64_t rows = (int64_t)nb * fast2d::kBandRows;
+                for (int64_t y = 0; y < d.dims[0]; y += rows) {
+                    items.push_back(BItem{f, 0, nb, (int)y, (int)std::min<int64_t>(y + rows, d.dims[0])});
                     cnt++;
                 }
+            } else {
+                for (int64_t y = 0; y < d.dims[0]; y += 64)
+                    for (int64_t x = 0; x < d.dims[1]; x += fast2d::SW) {
+                        items.push_back(BItem{f, (int)x, 0, (int)y, (int)std::min<int64_t>(y + 64, d.dims[0])});
+                        cnt++;
+                    }
+            }
         }
         F.nitems = cnt;
         bf.push_back(F);

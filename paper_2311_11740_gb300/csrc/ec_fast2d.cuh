@@ -32,6 +32,26 @@ constexpr int raw_pad() { return 16 / (int)sizeof(T); }
 template <typename T>
 constexpr int raw_bytes() { return (SW + 2 * raw_pad<T>()) * (int)sizeof(T); }
 
+// Banded strips (cover staging only): a field at most ~SW/nb - 2 pixels wide
+// is walked as nb row bands of kBandRows rows side by side in one strip, each
+// in its own SW/nb-pixel segment; the pixels between a band's right edge and
+// the next segment are never active, so the bands do not touch, and each
+// band's halo rows are its true neighbour rows.
+constexpr int kBandRows = 64;
+static_assert(SW == 1024, "banded segments are 256 or 512 pixels");
+template <typename T>
+constexpr int band_seg_bytes(int nb) { return (raw_bytes<T>() / nb) & ~15; }
+// Widest field that nb bands fit (0 if none): a band's 16-byte cover must fit
+// its segment and leave at least two never-active pixels before the next band.
+template <typename T>
+constexpr int band_max_width(int nb)
+{
+    return nb <= 1 ? 0
+                   : ((band_seg_bytes<T>(nb) - 15) / (int)sizeof(T) < SW / nb - 2
+                          ? (band_seg_bytes<T>(nb) - 15) / (int)sizeof(T)
+                          : SW / nb - 2);
+}
+
 struct Params {
     const void *field;
     int64_t H, W;
@@ -56,6 +76,8 @@ struct Ctx2 {
     IBin<T> ib;
     int x0, y0, y1;
     bool interior;
+    int nb = 1;          // row bands side by side in the strip (banded walk when > 1)
+    int64_t yb0 = 0;     // first field row of band 0; band b, virtual row v -> row yb0 + b*kBandRows + v
 };
 
 template <typename T>
@@ -197,17 +219,60 @@ using fast3d::cp_async16;
 using fast3d::cp_async_commit;
 using fast3d::cp_async_wait;
 
+// Banded copies of virtual row y: band b's field row yb0 + b*kBandRows + y
+// (its 16-byte cover) into segment b of the raw slot.
+template <typename T>
+__device__ __forceinline__ void copy_row_bands(const Ctx2<T> &c, int64_t y)
+{
+    constexpr int sz = (int)sizeof(T);
+    const int seg = band_seg_bytes<T>(c.nb), cps = seg / 16;
+    unsigned char *slot = c.raw + (uint32_t)((y + 16) % NRAW) * raw_bytes<T>();
+    const unsigned char *fb = (const unsigned char *)c.p.field;
+    const int64_t total = c.p.H * c.p.W * sz;
+    for (int q = threadIdx.x; q < c.nb * cps; q += kThreads) {
+        const int b = q / cps, ch = q - b * cps;
+        const int64_t yo = c.yb0 + (int64_t)b * kBandRows + y;
+        if (yo < 0 || yo >= c.p.H) continue;
+        const int64_t rs = yo * c.p.W * sz, cs = (rs & ~(int64_t)15) + 16 * ch;
+        if (cs >= rs + c.p.W * sz) continue;
+        const int64_t left = total - cs;
+        cp_async16(fast3d::smem_u32(slot + b * seg + ch * 16), fb + cs, left < 16 ? (uint32_t)left : 16u);
+    }
+}
+
+// Levels of virtual pixels x, x+1 (x even; strip coordinates, x0 = 0) of
+// banded virtual row y as one key word.  Segments are 2^sh pixels wide (256
+// or 512), so both pixels lie in one segment.
+template <typename T>
+__device__ __forceinline__ uint32_t band_word(Ctx2<T> &c, const unsigned char *raw, int64_t y, int x, int sh)
+{
+    constexpr int sz = (int)sizeof(T);
+    const uint32_t L = (uint32_t)c.p.L;
+    if (x < 0 || x >= SW) return L | (L << 16);
+    const int b = x >> sh, xl = x & ((1 << sh) - 1);
+    const int64_t yo = c.yb0 + (int64_t)b * kBandRows + y;
+    if (xl >= c.p.W || yo < 0 || yo >= c.p.H) return L | (L << 16);
+    const unsigned char *r = raw + b * band_seg_bytes<T>(c.nb) + (int)((yo * c.p.W * sz) & 15) + xl * sz;
+    const uint32_t b0 = bin_value2(c, *(const T *)r);
+    const uint32_t b1 = xl + 1 < c.p.W ? bin_value2(c, *(const T *)(r + sz)) : L;
+    return b0 | (b1 << 16);
+}
+
 // Start this thread's copies of row y (empty if y is beyond the item) and
 // close them as one group.  STG_ALIGNED: the row width and start are
 // multiples of 16 bytes, so a chunk lies wholly inside or wholly outside the
 // field.  STG_COVER (rows of any width, field start 16-byte aligned): the
 // 16-byte aligned cover of the row's in-field part of x0-2 .. x0+SW+1, the
 // field's last chunk clipped to its end.
-template <typename T, int STG>
+template <typename T, int STG, bool BANDED = false>
 __device__ __forceinline__ void copy_row(const Ctx2<T> &c, int64_t y, bool wanted)
 {
     constexpr int A = raw_pad<T>(), NCH = raw_bytes<T>() / 16, sz = (int)sizeof(T);
-    if (wanted && y >= 0 && y < c.p.H) {
+    if (!wanted) {
+        // nothing: rows past the item
+    } else if constexpr (BANDED) {
+        copy_row_bands<T>(c, y);
+    } else if (y >= 0 && y < c.p.H) {
         unsigned char *slot = c.raw + (uint32_t)((y + 16) % NRAW) * raw_bytes<T>();
         if constexpr (STG == fast3d::STG_ALIGNED) {
             const T *base = (const T *)c.p.field;
@@ -234,7 +299,7 @@ __device__ __forceinline__ void copy_row(const Ctx2<T> &c, int64_t y, bool wante
 
 // Bin row y from its raw slot into ring slot (y mod NR); pixels outside the
 // field bin to L.
-template <typename T, int STG>
+template <typename T, int STG, bool BANDED = false>
 __device__ __forceinline__ void bin_row_raw(Ctx2<T> &c, int64_t y)
 {
     constexpr int A = raw_pad<T>(), sz = (int)sizeof(T);
@@ -243,6 +308,15 @@ __device__ __forceinline__ void bin_row_raw(Ctx2<T> &c, int64_t y)
     const uint32_t L = (uint32_t)c.p.L;
     const bool yin = y >= 0 && y < c.p.H;
     const int64_t xlo = max((int64_t)c.x0 - 2, (int64_t)0);
+    if constexpr (BANDED) {
+        const int sh = c.nb == 4 ? 8 : 9;   // log2 of SW / nb (nb is 2 or 4)
+#pragma unroll
+        for (int it = 0; it < (RWORDS + kThreads - 1) / kThreads; it++) {
+            const int w = threadIdx.x + it * kThreads;
+            if (w < RWORDS) kr[w] = band_word(c, raw, y, 2 * w - 2, sh);
+        }
+        return;
+    }
     // byte of pixel x0-2 in the slot (may lie before the slot for the first strip: never read then)
     int64_t b0x;
     if constexpr (STG == fast3d::STG_ALIGNED) b0x = (int64_t)(A - 2) * sz;
@@ -264,12 +338,12 @@ __device__ __forceinline__ void bin_row_raw(Ctx2<T> &c, int64_t y)
 // Asynchronous row step, y = y0 - 2 + t: bin row y+1 (its copies finished
 // before the previous barrier), start the copies of row y+2+KA, wait for
 // this thread's copies of row y+2, synchronise, then count as ystep does.
-template <typename T, bool CONN4, int R, int DM, int STG>
+template <typename T, bool CONN4, int R, int DM, int STG, bool BANDED>
 __device__ __forceinline__ void ystep_async(Ctx2<T> &c, uint32_t (&win)[3][5], int t)
 {
     const int y = c.y0 - 2 + t;
-    bin_row_raw<T, STG>(c, y + 1);
-    copy_row<T, STG>(c, y + 2 + KA, y + 2 + KA <= c.y1);
+    bin_row_raw<T, STG, BANDED>(c, y + 1);
+    copy_row<T, STG, BANDED>(c, y + 2 + KA, y + 2 + KA <= c.y1);
     cp_async_wait<KA>();
     __syncthreads();
     count_row<T, CONN4, R, DM>(c, win, y);
@@ -290,17 +364,17 @@ __device__ __forceinline__ void walk_item_2d(Ctx2<T> &c, uint32_t (&win)[3][5])
 }
 
 // Asynchronous walk of one item (same rows as walk_item_2d).
-template <typename T, bool CONN4, int DM, int STG>
+template <typename T, bool CONN4, int DM, int STG, bool BANDED = false>
 __device__ __forceinline__ void walk_item_2d_async(Ctx2<T> &c, uint32_t (&win)[3][5])
 {
-    for (int q = 0; q <= KA; q++) copy_row<T, STG>(c, c.y0 - 1 + q, c.y0 - 1 + q <= c.y1);
+    for (int q = 0; q <= KA; q++) copy_row<T, STG, BANDED>(c, c.y0 - 1 + q, c.y0 - 1 + q <= c.y1);
     cp_async_wait<KA>();
     __syncthreads();
     const int nsteps = c.y1 - c.y0 + 2;
     for (int t = 0; t < nsteps; t += 3) {
-        ystep_async<T, CONN4, 0, DM, STG>(c, win, t);
-        if (t + 1 < nsteps) ystep_async<T, CONN4, 1, DM, STG>(c, win, t + 1);
-        if (t + 2 < nsteps) ystep_async<T, CONN4, 2, DM, STG>(c, win, t + 2);
+        ystep_async<T, CONN4, 0, DM, STG, BANDED>(c, win, t);
+        if (t + 1 < nsteps) ystep_async<T, CONN4, 1, DM, STG, BANDED>(c, win, t + 1);
+        if (t + 2 < nsteps) ystep_async<T, CONN4, 2, DM, STG, BANDED>(c, win, t + 2);
     }
     cp_async_wait<0>();
 }

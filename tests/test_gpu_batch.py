@@ -1,6 +1,8 @@
 """ec_batch: one persistent launch over uneven 2D/3D fields of mixed dtypes,
 level counts and descriptor sets gives, field by field, the curves of
 separate calls and of the oracle."""
+import zlib
+
 import numpy as np
 import pytest
 import torch
@@ -80,6 +82,32 @@ def test_batch_equals_oracle_and_single_calls(ctx, seed):
                          ctx=ctx)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(g, alone.cpu().numpy())
+
+
+# Narrow 2D fields share a strip between 4 (or 2) row bands of 64 rows; the
+# widths sit at and just past the limits (uint8 241 / 510, uint16 248, float32
+# 252), the heights cut bands and items anywhere.
+@pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
+def test_batch_banded_narrow_2d_fields(ctx, dtype):
+    rng = np.random.default_rng(zlib.crc32(dtype.encode()))
+    widths = {"u8": [1, 2, 63, 241, 242, 300, 510, 511], "u16": [3, 248, 249, 510, 511],
+              "f32": [5, 252, 253, 509, 510]}[dtype]
+    heights = [65, 128, 129, 255, 257, 300, 513]
+    fields = []
+    for i, w in enumerate(widths):
+        h = heights[i % len(heights)]
+        g = workloads.grf_2d(int(rng.integers(1 << 30)), h, w, 3.0).numpy()
+        if dtype == "u8":
+            f, thr, L = workloads.quantize_u8(torch.from_numpy(g)).numpy(), None, 256
+        elif dtype == "u16":
+            f, thr, L = np.clip(g * 500 + 1500, 0, 3000).astype(np.uint16), None, 3001
+        else:
+            f = g.astype(np.float32)
+            thr, L = np.linspace(f.min(), f.max(), 200).astype(np.float32), 200
+        fields.append(dict(field=f, thr=thr, L=L, conn=[8, 4][i % 2], desc=7))
+    got, _ = _run_batch(ctx, fields)
+    for f, g in zip(fields, got):
+        np.testing.assert_array_equal(g, oracle.ec_curves(f["field"], f["thr"], f["L"], f["conn"], f["desc"]))
 
 
 def test_batch_repeated_calls_reuse_graph(ctx):
