@@ -162,6 +162,7 @@ __device__ void item_3d(const BField &F, const BItem &it, const Shared &S, const
     c.interior = c.x0 >= 4 && c.x0 + TXF + 4 <= c.p.W;
     c.base = 0;
     c.parity = 0;
+    c.inflight = 0;
     uint32_t win[3][3][5];
 #pragma unroll
     for (int a = 0; a < 3; a++)

@@ -168,6 +168,7 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
     c.tc = threadIdx.x & 15;
     c.bin3 = bin3_offsets(threadIdx.x);
     c.parity = 0;
+    c.inflight = 0;
     uint32_t seq = 0;
     const int nitems = p.nbx * p.nby * p.nbz;
     uint32_t win[3][3][5];
@@ -196,6 +197,7 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
                     const uint32_t slot = (c.base + q) % NS;
                     mbar_expect_tx(&c.bars[slot], BX * BY * 4);
                     tma_load_plane(c.fring + slot * FSTRIDE, &tmap, c.x0 - 4, c.y0 - 1, pz, &c.bars[slot]);
+                    c.inflight |= 1u << slot;
                 }
             }
             const int nsteps = c.z1 - c.z0 + 4;

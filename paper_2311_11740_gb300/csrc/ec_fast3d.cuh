@@ -76,9 +76,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
-// Bounded wait for the phase with the given parity: gives up after about a
-// second of device time.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// Bounded wait for the phase with the given parity: gives up after `limit`
+// clock cycles (default: about two seconds).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = 4000000000ll)
 {
     const uint32_t addr = smem_u32(bar);
     const long long t0 = clock64();
@@ -92,7 +92,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
             : "r"(addr), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > 4000000000ll) break;
+        if (clock64() - t0 > limit) break;
     }
     return false;
 }
@@ -233,6 +233,7 @@ struct Ctx {
     int x0, y0, z0, z1;
     uint32_t base;
     uint32_t parity;
+    uint32_t inflight;         // thread 0: ring slots with a TMA copy issued and not yet waited for
     bool interior;
 };
 
@@ -598,6 +599,19 @@ __device__ __forceinline__ bool zstep(Ctx<T> &c, uint32_t (&win)[3][3][5], int t
     return true;
 }
 
+// After a wait gave up: wait (bounded, about half a second each) for the
+// block's other TMA copies still in flight, so none lands after the block
+// has left.
+template <typename T>
+__device__ __forceinline__ void drain_tma(Ctx<T> &c)
+{
+    for (int slot = 0; slot < NS; slot++)
+        if ((c.inflight >> slot) & 1u) {
+            mbar_wait(&c.bars[slot], (c.parity >> slot) & 1u, 1000000000ll);
+            c.inflight &= ~(1u << slot);
+        }
+}
+
 // One half-step of the TMA z walk (float32 fields), counting plane
 // h = z0 - 4 + t.  Every other half-step (t even) is a barrier step: thread 0
 // waits for the staged float planes h+3 and h+4, the block synchronises,
@@ -622,12 +636,17 @@ __device__ __forceinline__ bool zstep_tma(Ctx<T> &c, const CUtensorMap *tmap, ui
                 if (!mbar_wait(&c.bars[slot], (c.parity >> slot) & 1u)) {
                     *c.abort_flag = 1;
                     atomicOr(c.p.err, 4);
+                    break;
                 }
                 c.parity ^= 1u << slot;
+                c.inflight &= ~(1u << slot);
             }
         }
         __syncthreads();
-        if (*c.abort_flag) return false;
+        if (*c.abort_flag) {
+            if (threadIdx.x == 0) drain_tma(c);
+            return false;
+        }
         if (threadIdx.x == 0) {
 #pragma unroll
             for (int q = NS + 1; q <= NS + 2; q++) {
@@ -636,6 +655,7 @@ __device__ __forceinline__ bool zstep_tma(Ctx<T> &c, const CUtensorMap *tmap, ui
                 const uint32_t slot = (c.base + (uint32_t)(pi - (c.z0 - 1))) % NS;
                 mbar_expect_tx(&c.bars[slot], BX * BY * 4);
                 tma_load_plane(c.fring + slot * FSTRIDE, tmap, c.x0 - 4, c.y0 - 1, pi, &c.bars[slot]);
+                c.inflight |= 1u << slot;
             }
         }
         // ---- bin planes h+3 (extra pairs on threads 0-99) and h+4 (threads 128-227)
