@@ -8,7 +8,8 @@ The arithmetic lives in ``ec_oracle.c`` (plain cell counting of the closed
 cubical complex; see that file's header for the definitions it follows and the
 paper passages they come from).  This module compiles it with gcc/OpenMP and
 wraps it with ctypes and numpy.  ``brute.py`` holds the literal per-level
-enumeration used to pin the oracle on tiny grids.
+enumeration used to pin the oracle on tiny grids; ``typemap.py`` counts the
+vertex types of Tables 1 and 2 at every level (the contribution-type map).
 """
 from __future__ import annotations
 
