@@ -255,6 +255,51 @@ int ec_server_wait_all(ec_server *server, int64_t timeout_ms);
 int ec_server_reset_stats(ec_server *server);
 int ec_server_destroy(ec_server *server);
 
+/* ----------------------------------------------- contribution-type map
+ * The paper's full output (Sec. 2, Algorithm 1 and Table 1; Sec. 2.2,
+ * Algorithm 3 and Table 2; Sec. 4): how many grid vertices have each
+ * contribution type at each level.  A field of h x w pixels has (h+1)(w+1)
+ * vertices, one of d x h x w voxels (d+1)(h+1)(w+1); a vertex's type is the
+ * class (under the symmetries of the square / cube) of the set of active
+ * cells among the 2^n cells around it, cells outside the field never active.
+ * Types are numbered by the tables' rows from 0:
+ *   2D (EC_NTYPES_2D = 6): Q0 (empty), Q1, Q2 (two pixels sharing an edge),
+ *      QD (two diagonal pixels), Q3, Q4;
+ *   3D (EC_NTYPES_3D = 22): the rows of Table 2 in printed order, 0 = empty,
+ *      21 = all eight voxels (ec_type_table gives the type of every mask).
+ * The types do not depend on connectivity; only the weights do. */
+#define EC_NTYPES_2D 6
+#define EC_NTYPES_3D 22
+
+/* counts_dev: int64 [T][L] on the device, T = EC_NTYPES_2D or _3D;
+ * counts[t][k] = number of vertices of type t at level k (active iff the
+ * cell's bin is <= k, bins as for ec_curve_2d / ec_curve_3d).  Every column
+ * sums to the number of vertices.  ndim = 2 (dims {h, w}) or 3 (dims
+ * {d, h, w}); field, dtype, thresholds and L as in ec_curve_2d/3d.  Stream
+ * ordered; uses the context's scratch ((T-1) * L * 8 bytes + 256).  With
+ * EC_OPT_PROFILE the histogram kernel is timed like a curve request's. */
+int ec_type_map(ec_ctx *ctx, int32_t ndim, const void *field_dev, const int64_t *dims, int dtype,
+                const void *thresholds_dev, int32_t L, int64_t *counts_dev, void *stream);
+
+/* Weighted curves from a type map (Sec. 4: any descriptor that is a weighted
+ * sum of vertex contributions):
+ *   out[d][k] = sum_t weights[d][t] * counts[t][k] / scales[d]
+ * counts_dev: int64 [ntypes][L] (device); weights_host: int32 [nd][ntypes]
+ * (host, row-major); scales_host: int32 [nd] >= 1, or NULL for all 1;
+ * out_dev: int64 [nd][L] (device).  1 <= ntypes <= 22, 1 <= nd <= 16.
+ * Sums are exact (128-bit); an entry whose sum is not a multiple of its
+ * scale, or does not fit int64, is written as INT64_MIN, and with
+ * EC_OPT_VALIDATE the call then returns EC_ERR_ARG (it synchronises the
+ * stream to find out).  Example: Table 2's columns times 8, 2, 4, 8 with
+ * scales {8, 2, 4, 8} give ec_curve_3d's EC, perimeter, area and volume. */
+int ec_apply_weights(ec_ctx *ctx, int32_t ntypes, const int64_t *counts_dev, int32_t L, int32_t nd,
+                     const int32_t *weights_host, const int32_t *scales_host, int64_t *out_dev, void *stream);
+
+/* Type of every neighbourhood mask (host): ndim 2 -> out[16], ndim 3 ->
+ * out[256]; mask bit x + 2y (+ 4z) for the cell at offset (x, y[, z]) in
+ * {0,1}^n from the vertex's lower corner, x the fastest field axis. */
+int ec_type_table(int32_t ndim, int32_t *out);
+
 /* ---------------------------------------------------- host-side inspection
  * The per-vertex contribution tables the kernels use, derived at build time
  * from the closed-complex rule (Tables 1 and 2 of the paper are what they

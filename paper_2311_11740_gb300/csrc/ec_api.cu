@@ -461,6 +461,22 @@ int64_t ec_selfcheck_rules(void)
             if (ec[v] != d.ec || pe[v] != d.per || ar[v] != d.area) bad++;
         }
     }
+    // vertex types: every mask has a row, and the per-mask contributions are
+    // the same for every mask of a type (the tables' premise)
+    {
+        constexpr TypeTable2D tt2 = make_type_table_2d();
+        constexpr TypeTable3D tt3 = make_type_table_3d();
+        for (unsigned m = 0; m < 16; m++) {
+            if (tt2.t[m] >= kTypes2) { bad++; continue; }
+            const unsigned r = kTable1Reps[tt2.t[m]];
+            for (int k = 0; k < 4; k++) bad += t2.v[m][k] != t2.v[r][k];
+        }
+        for (unsigned m = 0; m < 256; m++) {
+            if (tt3.t[m] >= kTypes3) { bad++; continue; }
+            const unsigned r = kTable2Reps[tt3.t[m]];
+            for (int k = 0; k < 4; k++) bad += t3.v[m][k] != t3.v[r][k];
+        }
+    }
     return bad;
 }
 

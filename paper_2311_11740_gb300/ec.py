@@ -81,6 +81,9 @@ def lib():
             L.ec_server_destroy.argtypes = [P]
             L.ec_tuned_plan.argtypes = [P, I32, ctypes.c_int, I32, U32, ctypes.POINTER(I64), ctypes.POINTER(I32)]
             L.ec_gen_hashbox_u16.argtypes = [ctypes.c_uint64, I64, I64, I64, I64, I64, I64, P, P]
+            L.ec_type_map.argtypes = [P, I32, P, ctypes.POINTER(I64), ctypes.c_int, P, I32, P, P]
+            L.ec_apply_weights.argtypes = [P, I32, P, I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), P, P]
+            L.ec_type_table.argtypes = [I32, P]
             _lib = L
     return _lib
 
@@ -393,6 +396,64 @@ def hashbox_stream(spec: HashboxSpec, nz: int, thresholds=None, L=4096, descript
     _check(lib().ec_curve_3d_stream(ctx.handle, None, cb, ctypes.c_void_p(user), _dims(dims), EC_U16,
                                     ctypes.c_void_p(thr_ptr), int(L), 26, int(descriptors), int(slab_planes),
                                     ctypes.c_size_t(int(device_mem_cap)), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+NTYPES = {2: 6, 3: 22}
+
+
+def type_map(field, thresholds=None, L=None, out=None, ctx: Context | None = None, stream=None):
+    """Contribution-type map of a CUDA tensor field (ec_type_map): int64 CUDA
+    tensor [T, L], counts[t][k] = vertices of type t (Table 1 / Table 2 row
+    order) at level k."""
+    import torch
+    assert field.is_cuda and field.is_contiguous(), "field must be a contiguous CUDA tensor"
+    dev = field.device.index if field.device.index is not None else torch.cuda.current_device()
+    ctx = ctx or default_context(dev)
+    if thresholds is not None:
+        assert thresholds.is_cuda and thresholds.dtype == field.dtype and thresholds.is_contiguous()
+        L = thresholds.numel() if L is None else L
+    if L is None:
+        raise ValueError("L is required with identity levels")
+    ndim = field.dim()
+    if ndim not in NTYPES:
+        raise ValueError("field must be 2D or 3D")
+    if out is None:
+        out = torch.empty((NTYPES[ndim], L), dtype=torch.int64, device=field.device)
+    _check(lib().ec_type_map(ctx.handle, ndim, ctypes.c_void_p(field.data_ptr()), _dims(field.shape),
+                             dtype_code(field),
+                             ctypes.c_void_p(thresholds.data_ptr() if thresholds is not None else 0), int(L),
+                             ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream, dev)))
+    return out
+
+
+def apply_weights(counts, weights, scales=None, out=None, ctx: Context | None = None, stream=None):
+    """Weighted curves from a type map (ec_apply_weights): out[d][k] =
+    sum_t weights[d][t] counts[t][k] / scales[d]; counts an int64 CUDA tensor
+    [T, L], weights an integer array [nd, T]."""
+    import torch
+    assert counts.is_cuda and counts.dtype == torch.int64 and counts.is_contiguous()
+    dev = counts.device.index if counts.device.index is not None else torch.cuda.current_device()
+    ctx = ctx or default_context(dev)
+    W = np.ascontiguousarray(np.asarray(weights, dtype=np.int32))
+    if W.ndim != 2 or W.shape[1] != counts.shape[0]:
+        raise ValueError("weights must be [nd, T]")
+    nd, T = W.shape
+    L = counts.shape[1]
+    sc = None if scales is None else np.ascontiguousarray(np.asarray(scales, dtype=np.int32))
+    if out is None:
+        out = torch.empty((nd, L), dtype=torch.int64, device=counts.device)
+    I32P = ctypes.POINTER(ctypes.c_int32)
+    _check(lib().ec_apply_weights(ctx.handle, T, ctypes.c_void_p(counts.data_ptr()), L, nd,
+                                  W.ctypes.data_as(I32P), None if sc is None else sc.ctypes.data_as(I32P),
+                                  ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream, dev)))
+    return out
+
+
+def type_table(ndim: int) -> np.ndarray:
+    """Type of every neighbourhood mask (bit x + 2y (+ 4z)), from the library."""
+    out = np.zeros(1 << (1 << ndim), np.int32)
+    _check(lib().ec_type_table(ndim, out.ctypes.data_as(ctypes.c_void_p)))
     return out
 
 

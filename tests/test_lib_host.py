@@ -69,3 +69,25 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
         assert "missing" in str(e)
     else:
         raise AssertionError("expected a failure")
+
+
+def test_type_tables_match_the_oracle_classifier(libec):
+    """The library's mask -> type tables (Table 1/2 pictures closed under the
+    square/cube symmetries) equal the oracle's count-and-f_adj classifier."""
+    from oracle import typemap as tm
+    from paper_2311_11740_gb300 import ec
+    for ndim in (2, 3):
+        np.testing.assert_array_equal(ec.type_table(ndim), tm.type_table(ndim))
+
+
+def test_type_table_rows_carry_the_paper_weights(libec):
+    """Every mask of a type has the type's Table 2 weights (the table the
+    kernels use agrees with the printed row of the mask's type)."""
+    from paper_2311_11740_gb300 import ec
+    tt = ec.type_table(3)
+    _, by_class = _tables.table2()
+    rows = {r["row"] - 1: r for r in by_class.values()}
+    vt = ec.vertex_table_3d()
+    for m in range(256):
+        r = rows[int(tt[m])]
+        assert Fraction(int(vt[m, 0]), 8) == r["EC"] and Fraction(int(vt[m, 3]), 8) == r["Volume"], m
