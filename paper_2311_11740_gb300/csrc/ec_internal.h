@@ -78,10 +78,6 @@ int launch_uniform_check(const float *thr, int32_t L, int *uni, cudaStream_t s);
 int launch_scan(const long long *hist, int nd, int32_t L, const int32_t scale[kMaxDesc],
                 int64_t *out, int *err_flag, cudaStream_t s);
 int launch_check_sorted(const void *thr, int dtype, int32_t L, int *flag, cudaStream_t s);
-// Vertex-type histogram (transitions per level, types 1..T-1 as int64
-// [T-1][L], zeroed by the caller) of a 2D or 3D field.
-int launch_type_map(int ndim, const void *field, const int64_t *dims, const BinArgs &ba, long long *hist,
-                    int tile_z, int grid, int num_sms, cudaStream_t s);
 
 // Scale of each descriptor row for an algorithm (1 for the per-top-cell path,
 // the table scales for the per-vertex path).
@@ -90,8 +86,6 @@ void row_scales(int ndim, int algo, uint32_t desc, int32_t out[kMaxDesc]);
 // Shared-memory budget for the block-private histogram.
 constexpr size_t kSmemHistBudget = 96 * 1024;
 inline bool use_smem_hist(int nd, int32_t L) { return (size_t)nd * ((size_t)L + 1) * 4 <= kSmemHistBudget; }
-// Shared-memory budget of the block-private type histogram (int32 [L][T]).
-constexpr size_t kSmemTypeHistBudget = 96 * 1024;
 
 enum { ALGO_AUTO = 0, ALGO_VOXEL = 1, ALGO_VERTEX = 2 };
 

@@ -441,161 +441,6 @@ __global__ void __launch_bounds__(kThreads) k_vertex2d(const T *__restrict__ f, 
     flush_hist(hist, ha.rows.nd);
 }
 
-// ------------------------------------------------------- vertex type map
-//
-// Contribution-type map (the born/dies arrays of Algorithms 1-3, Sec. 2 and
-// 2.2): per vertex, sort the 2^n (level, position) keys of its neighbourhood
-// and walk them.  At each distinct level b < L the vertex's type changes from
-// the type of its cells below b to the type of its cells at or below b: +1 for
-// the new type and -1 for the old one, both at b.  Equal levels are merged, so
-// the running sums are the plain numbers of vertices of each type at each
-// level.  The empty type 0 is never written; it is back-calculated from the
-// number of vertices (Sec. 2.1).
-
-__constant__ TypeTable2D c_type2 = make_type_table_2d();
-__constant__ TypeTable3D c_type3 = make_type_table_3d();
-
-template <int NT>
-struct TypeHist {
-    int *sh;          // shared int32 [L][NT] (type fastest), or nullptr
-    long long *g;     // global int64 [NT-1][L]: types 1..NT-1
-    int L;
-
-    __device__ __forceinline__ void add(uint32_t bin, int t, int v) const
-    {
-        if (sh) atomicAdd(&sh[bin * NT + t], v);
-        else atomicAdd((unsigned long long *)&g[(size_t)(t - 1) * L + bin], (unsigned long long)(long long)v);
-    }
-    __device__ void init()
-    {
-        if (sh)
-            for (int i = threadIdx.x; i < L * NT; i += blockDim.x) sh[i] = 0;
-    }
-    __device__ void flush() const
-    {
-        if (!sh) return;
-        __syncthreads();
-        for (int i = threadIdx.x; i < L * NT; i += blockDim.x) {
-            const int v = sh[i];
-            const int t = i % NT, b = i / NT;
-            if (v && t) atomicAdd((unsigned long long *)&g[(size_t)(t - 1) * L + b], (unsigned long long)(long long)v);
-        }
-    }
-};
-
-__host__ __device__ inline size_t type_hist_smem_bytes(int L, int nt)
-{
-    return (((size_t)L * nt * 4) + 15) & ~(size_t)15;
-}
-
-// Emit the transitions of one vertex from its sorted keys (level << SH | position).
-template <int NK, int SH, int NT>
-__device__ __forceinline__ void walk_types(const uint32_t (&s)[NK], uint32_t L, const uint8_t *tl,
-                                           const TypeHist<NT> &h)
-{
-    uint32_t cur = s[0] >> SH;
-    if (cur >= L) return;
-    unsigned m = 1u << (s[0] & ((1u << SH) - 1u));
-    int tprev = 0;
-#pragma unroll
-    for (int j = 1; j < NK; j++) {
-        const uint32_t b = s[j] >> SH;
-        if (b != cur) {
-            const int t = tl[m];
-            h.add(cur, t, 1);
-            if (tprev) h.add(cur, tprev, -1);
-            tprev = t;
-            cur = b;
-            if (cur >= L) return;
-        }
-        m |= 1u << (s[j] & ((1u << SH) - 1u));
-    }
-    const int t = tl[m];
-    h.add(cur, t, 1);
-    if (tprev) h.add(cur, tprev, -1);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_typemap3d(const T *__restrict__ f, Geom3 g, BinArgs ba,
-                                                        long long *ghist, int smem_hist)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const size_t hb = smem_hist ? type_hist_smem_bytes(ba.L, kTypes3) : 0;
-    TypeHist<kTypes3> hist{smem_hist ? (int *)smem : nullptr, ghist, ba.L};
-    hist.init();
-    const size_t bb = binner_smem_bytes<T>(ba.L, ba.thr != nullptr);
-    Binner<T> bin = make_binner<T>(ba, smem + hb);
-    uint8_t *tl = smem + hb + bb;
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) tl[i] = c_type3.t[i];
-    uint16_t *ring = (uint16_t *)(smem + hb + bb + 256);
-    const uint32_t L = (uint32_t)ba.L;
-    const int tx = threadIdx.x % TX3, ty = threadIdx.x / TX3;
-    const int nitems = g.nbx * g.nby * g.nbz;
-
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const int bx = item % g.nbx, by = (item / g.nbx) % g.nby, bz = item / (g.nbx * g.nby);
-        const int64_t x0 = (int64_t)bx * TX3, y0 = (int64_t)by * TY3;
-        const int64_t z0 = g.zc0 + (int64_t)bz * g.tz, z1 = min(z0 + g.tz, g.zc1);
-        __syncthreads();
-        stage_plane3<T>(ring + ((z0 + 3) & 3) * RS3, f, g, bin, z0 - 1, x0, y0);
-        const int64_t X = x0 + tx, Y = y0 + ty;
-        for (int64_t Z = z0; Z < z1; Z++) {
-            stage_plane3<T>(ring + ((Z + 4) & 3) * RS3, f, g, bin, Z, x0, y0);
-            __syncthreads();
-            if (X > g.W || Y > g.H) continue;
-            const uint16_t *rz[2] = {ring + ((Z + 3) & 3) * RS3, ring + ((Z + 4) & 3) * RS3};
-            uint32_t s[8];
-#pragma unroll
-            for (int b = 0; b < 8; b++) {
-                const int dx = b & 1, dy = (b >> 1) & 1, dz = b >> 2;
-                s[b] = ((uint32_t)rz[dz][(ty + dy) * RW3 + tx + dx] << 3) | (uint32_t)b;
-            }
-            sort8(s);
-            walk_types<8, 3, kTypes3>(s, L, tl, hist);
-        }
-    }
-    hist.flush();
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_typemap2d(const T *__restrict__ f, Geom2 g, BinArgs ba,
-                                                        long long *ghist, int smem_hist)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const size_t hb = smem_hist ? type_hist_smem_bytes(ba.L, kTypes2) : 0;
-    TypeHist<kTypes2> hist{smem_hist ? (int *)smem : nullptr, ghist, ba.L};
-    hist.init();
-    const size_t bb = binner_smem_bytes<T>(ba.L, ba.thr != nullptr);
-    Binner<T> bin = make_binner<T>(ba, smem + hb);
-    uint8_t *tl = smem + hb + bb;
-    for (int i = threadIdx.x; i < 16; i += blockDim.x) tl[i] = c_type2.t[i];
-    uint16_t *ring = (uint16_t *)(smem + hb + bb + 16);
-    const uint32_t L = (uint32_t)ba.L;
-    const int tx = threadIdx.x;
-    const int nitems = g.nbx * g.nby;
-    const int64_t NY = g.H + 1;
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-        const int bx = item % g.nbx, by = item / g.nbx;
-        const int64_t x0 = (int64_t)bx * TX2;
-        const int64_t y0 = (int64_t)by * g.ty, y1 = min(y0 + g.ty, NY);
-        __syncthreads();
-        stage_row2<T>(ring + ((y0 + 3) & 3) * RW2, f, g, bin, y0 - 1, x0);
-        const int64_t X = x0 + tx;
-        for (int64_t Y = y0; Y < y1; Y++) {
-            stage_row2<T>(ring + ((Y + 4) & 3) * RW2, f, g, bin, Y, x0);
-            __syncthreads();
-            if (X > g.W) continue;
-            const uint16_t *ry[2] = {ring + ((Y + 3) & 3) * RW2, ring + ((Y + 4) & 3) * RW2};
-            uint32_t s[4];
-#pragma unroll
-            for (int b = 0; b < 4; b++) s[b] = ((uint32_t)ry[b >> 1][tx + (b & 1)] << 2) | (uint32_t)b;
-            cswap(s[0], s[1]); cswap(s[2], s[3]); cswap(s[0], s[2]); cswap(s[1], s[3]); cswap(s[1], s[2]);
-            walk_types<4, 2, kTypes2>(s, L, tl, hist);
-        }
-    }
-    hist.flush();
-}
-
 // -------------------------------------------------------------- scan kernel
 
 struct Scales { int32_t s[kMaxDesc]; };
@@ -788,60 +633,6 @@ int launch_check_sorted(const void *thr, int dtype, int32_t L, int *flag, cudaSt
     else k_check_sorted_int<uint8_t><<<blocks, 256, 0, s>>>((const uint8_t *)thr, L, flag);
     EC_CUDA(cudaGetLastError());
     return EC_OK;
-}
-
-template <typename T>
-static int launch_types(int ndim, const void *field, const int64_t *dims, const BinArgs &ba, long long *hist,
-                        int tile_z, int grid_override, int num_sms, cudaStream_t s)
-{
-    const int nt = ndim == 2 ? kTypes2 : kTypes3;
-    const int smem_hist = type_hist_smem_bytes(ba.L, nt) <= kSmemTypeHistBudget ? 1 : 0;
-    const size_t common = (smem_hist ? type_hist_smem_bytes(ba.L, nt) : 0) +
-                          binner_smem_bytes<T>(ba.L, ba.thr != nullptr) + (ndim == 2 ? 16 : 256);
-    int grid = 0;
-    if (ndim == 3) {
-        Geom3 g;
-        g.D = dims[0]; g.H = dims[1]; g.W = dims[2];
-        g.vertex = 1;
-        g.zc0 = 0; g.zc1 = g.D + 1;
-        g.zv0 = 0; g.zv1 = g.D;
-        g.tz = tile_z > 0 ? tile_z : 32;
-        g.nbx = (int)((g.W + 1 + TX3 - 1) / TX3);
-        g.nby = (int)((g.H + 1 + TY3 - 1) / TY3);
-        g.nbz = (int)((g.D + 1 + g.tz - 1) / g.tz);
-        const int64_t items = (int64_t)g.nbx * g.nby * g.nbz;
-        if (items > INT32_MAX) { set_error("field too large for one launch"); return EC_ERR_UNSUPPORTED; }
-        const size_t smem = common + kRing * RS3 * sizeof(uint16_t);
-        int rc = prepare_kernel(k_typemap3d<T>, smem, num_sms, (int)items, grid_override, &grid);
-        if (rc) return rc;
-        k_typemap3d<T><<<grid, kThreads, smem, s>>>((const T *)field, g, ba, hist, smem_hist);
-    } else {
-        Geom2 g;
-        g.H = dims[0]; g.W = dims[1];
-        g.ty = 64;
-        g.nbx = (int)((g.W + 1 + TX2 - 1) / TX2);
-        g.nby = (int)((g.H + 1 + g.ty - 1) / g.ty);
-        const int64_t items = (int64_t)g.nbx * g.nby;
-        if (items > INT32_MAX) { set_error("field too large for one launch"); return EC_ERR_UNSUPPORTED; }
-        const size_t smem = common + kRing * RW2 * sizeof(uint16_t);
-        int rc = prepare_kernel(k_typemap2d<T>, smem, num_sms, (int)items, grid_override, &grid);
-        if (rc) return rc;
-        k_typemap2d<T><<<grid, kThreads, smem, s>>>((const T *)field, g, ba, hist, smem_hist);
-    }
-    EC_CUDA(cudaGetLastError());
-    return EC_OK;
-}
-
-int launch_type_map(int ndim, const void *field, const int64_t *dims, const BinArgs &ba, long long *hist,
-                    int tile_z, int grid, int num_sms, cudaStream_t s)
-{
-    switch (ba.dtype) {
-    case EC_U8: return launch_types<uint8_t>(ndim, field, dims, ba, hist, tile_z, grid, num_sms, s);
-    case EC_U16: return launch_types<uint16_t>(ndim, field, dims, ba, hist, tile_z, grid, num_sms, s);
-    case EC_F32: return launch_types<float>(ndim, field, dims, ba, hist, tile_z, grid, num_sms, s);
-    }
-    set_error("unknown dtype %d", ba.dtype);
-    return EC_ERR_DTYPE;
 }
 
 void row_scales(int ndim, int algo, uint32_t desc, int32_t out[kMaxDesc])

@@ -11,12 +11,422 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <type_traits>
+
+#include "ec_fast3d.cuh"   // fbin / IBin: level of a value (uniform-spacing guess, binary-search fallback)
 #include "ec_internal.h"
 #include "ec_rules.h"
 
 using namespace ec;
 
 namespace {
+
+// ------------------------------------------------------------ histogram kernel
+//
+// The born/dies arrays of Algorithms 1-3 (Sec. 2 and 2.2), per vertex: sort
+// the 2^n (level, position) keys of the vertex's neighbourhood and walk them
+// in order.  At each distinct level b < L the vertex's type changes from the
+// type of its cells below b to the type of its cells at or below b: +1 for
+// the new type and -1 for the old one, both at b.  Equal levels are merged,
+// so the running sums are the plain counts of vertices of each type at each
+// level.  The empty type 0 is never written; it is back-calculated from the
+// number of vertices (Sec. 2.1).
+//
+// A block stages the levels of one plane (3D) or row (2D) of cells at a
+// time into a ring of three slots, so one barrier per plane suffices, and
+// adds into a private shared-memory int32 histogram [L][stride] (odd row
+// strides spread a warp's levels over the banks) that is added into the
+// global int64 histogram [T-1][L] at the end.
+
+constexpr int kTmThreads = 512;
+constexpr int TX3 = 32, TY3 = 16, SW3 = TX3 + 1, SPLANE3 = SW3 * (TY3 + 1);   // 3D: vertices / staged cells
+constexpr int TX2 = 512, SW2 = TX2 + 1, TY2 = 64;                              // 2D: vertices per row, rows per tile
+constexpr int kStride3 = 23, kStride2 = 7;
+constexpr int kThrSmem = 4096;
+constexpr size_t kTypeHistBudget = 100 * 1024;
+
+__constant__ TypeTable2D c_types2 = make_type_table_2d();
+__constant__ TypeTable3D c_types3 = make_type_table_3d();
+
+template <typename T>
+struct TBin {
+    fast3d::FBin f;
+    fast3d::IBin<T> i;
+    __device__ __forceinline__ uint32_t operator()(T v) const
+    {
+        if constexpr (std::is_same<T, float>::value) return fast3d::fbin(v, f);
+        else return i(v);
+    }
+};
+
+template <typename T>
+__host__ __device__ constexpr size_t tbin_smem_bytes(int L, bool has_thr)
+{
+    return sizeof(T) == 1 ? 512 : ((has_thr && L <= kThrSmem) ? (((size_t)L * sizeof(T) + 15) & ~(size_t)15) : 0);
+}
+
+template <typename T>
+__device__ TBin<T> make_tbin(const T *gthr, int L, unsigned char *sm)
+{
+    TBin<T> b{};
+    if constexpr (std::is_same<T, float>::value) {
+        const float *t = gthr;
+        if (L <= kThrSmem) {
+            float *st = (float *)sm;
+            for (int k = threadIdx.x; k < L; k += blockDim.x) st[k] = gthr[k];
+            t = st;
+        }
+        b.f.t = t;
+        b.f.L = L;
+        b.f.t0 = gthr[0];
+        b.f.tl = gthr[L - 1];
+        b.f.inv = (L > 1 && b.f.tl > b.f.t0) ? (float)(L - 1) / (b.f.tl - b.f.t0) : 0.f;
+        b.f.off = 0.f;
+        b.f.lm1 = (float)(L - 1);
+        b.f.uniform = 0;
+    } else if constexpr (sizeof(T) == 1) {
+        uint16_t *tab = (uint16_t *)sm;
+        for (int v = threadIdx.x; v < 256; v += blockDim.x) {
+            int k;
+            if (!gthr) {
+                k = v < L ? v : L;
+            } else {
+                int lo = 0, n = L;
+                while (n > 0) {
+                    const int half = n >> 1;
+                    if ((int)gthr[lo + half] < v) { lo += half + 1; n -= half + 1; }
+                    else n = half;
+                }
+                k = lo;
+            }
+            tab[v] = (uint16_t)k;
+        }
+        b.i.table = tab;
+        b.i.t = nullptr;
+        b.i.L = L;
+    } else {
+        const T *t = gthr;
+        if (gthr && L <= kThrSmem) {
+            T *st = (T *)sm;
+            for (int k = threadIdx.x; k < L; k += blockDim.x) st[k] = gthr[k];
+            t = st;
+        }
+        b.i.table = nullptr;
+        b.i.t = t;
+        b.i.L = L;
+    }
+    return b;
+}
+
+struct G3 {
+    const void *f;
+    int D, H, W;                 // cells per axis
+    int nbx, nby, nbz, tz;       // vertex tiles, vertex planes per tile
+};
+struct G2 {
+    const void *f;
+    int H, W;
+    int nbx, nby;
+};
+
+// Vertex-type transitions of one vertex from its sorted keys (level << SH | position).
+template <int NK, int SH, int STRIDE, bool SMEM>
+__device__ __forceinline__ void walk_types(const uint32_t (&s)[NK], uint32_t L, const uint8_t *tl, int *sh,
+                                           long long *g)
+{
+    auto add = [&](uint32_t b, int t, int v) {
+        if constexpr (SMEM) atomicAdd(&sh[b * STRIDE + t], v);
+        else atomicAdd((unsigned long long *)&g[(size_t)(t - 1) * L + b], (unsigned long long)(long long)v);
+    };
+    uint32_t m = 0;
+    int tp = 0;
+#pragma unroll
+    for (int j = 0; j < NK; j++) {
+        const uint32_t b = s[j] >> SH;
+        m |= 1u << (s[j] & ((1u << SH) - 1u));
+        // sorted keys: the next key has another level iff the xor reaches the level bits
+        const bool boundary = j + 1 == NK || (s[j + 1 < NK ? j + 1 : j] ^ s[j]) >= (1u << SH);
+        if (boundary && b < L) {
+            const int t = tl[m];
+            add(b, t, 1);
+            if (tp) add(b, tp, -1);
+            tp = t;
+        }
+    }
+}
+
+template <int NT, int STRIDE>
+__device__ void flush_types(const int *sh, long long *g, int L)
+{
+    __syncthreads();
+    for (int i = threadIdx.x; i < L * STRIDE; i += blockDim.x) {
+        const int t = i % STRIDE, b = i / STRIDE;
+        const int v = sh[i];
+        if (v && t > 0 && t < NT) atomicAdd((unsigned long long *)&g[(size_t)(t - 1) * L + b], (unsigned long long)(long long)v);
+    }
+}
+
+// Staging of the (TX3+1) x (TY3+1) cells of a plane with lower corner
+// (x0-1, y0-1): thread t stages cells t and t + 512 of the plane (row-major,
+// TX3+1 wide).  Offsets within a plane are fixed per tile; each plane's raw
+// values are loaded one plane ahead into registers so that the loads are in
+// flight during the barrier and the walk.  Cells outside the field get L.
+template <typename T>
+struct Stage3 {
+    int64_t off[2];
+    bool ok[2];
+    T raw[2];
+    bool zin;
+    static constexpr int kPer = (SPLANE3 + kTmThreads - 1) / kTmThreads;
+
+    __device__ __forceinline__ void setup(const G3 &g, int x0, int y0)
+    {
+#pragma unroll
+        for (int q = 0; q < kPer; q++) {
+            const int i = threadIdx.x + q * kTmThreads;
+            const int ly = i / SW3, lx = i - ly * SW3;
+            const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+            ok[q] = i < SPLANE3 && (unsigned)gx < (unsigned)g.W && (unsigned)gy < (unsigned)g.H;
+            off[q] = ok[q] ? (int64_t)gy * g.W + gx : 0;
+        }
+    }
+    __device__ __forceinline__ void load(const G3 &g, int z)
+    {
+        zin = z >= 0 && z < g.D;
+        const T *plane = (const T *)g.f + (zin ? (int64_t)z * g.H * g.W : 0);
+#pragma unroll
+        for (int q = 0; q < kPer; q++)
+            if (ok[q] && zin) raw[q] = __ldg(plane + off[q]);
+    }
+    __device__ __forceinline__ void store(uint16_t *slot, const TBin<T> &bin, uint32_t L) const
+    {
+#pragma unroll
+        for (int q = 0; q < kPer; q++) {
+            const int i = threadIdx.x + q * kTmThreads;
+            if (i < SPLANE3) slot[i] = (uint16_t)((ok[q] && zin) ? bin(raw[q]) : L);
+        }
+    }
+};
+
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(kTmThreads, 2) k_types3(G3 g, const T *thr, int L, long long *ghist)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const size_t hb = SMEM ? (((size_t)L * kStride3 * 4 + 15) & ~(size_t)15) : 0;
+    int *sh = (int *)smem;
+    const size_t bb = tbin_smem_bytes<T>(L, thr != nullptr);
+    uint8_t *tl = smem + hb + bb;
+    uint16_t *ring = (uint16_t *)(smem + hb + bb + 256);
+    if (SMEM)
+        for (int i = threadIdx.x; i < L * kStride3; i += kTmThreads) sh[i] = 0;
+    for (int i = threadIdx.x; i < 256; i += kTmThreads) tl[i] = c_types3.t[i];
+    const TBin<T> bin = make_tbin<T>(thr, L, smem + hb);
+    __syncthreads();
+    const uint32_t UL = (uint32_t)L;
+    const int tx = threadIdx.x % TX3, ty = threadIdx.x / TX3;
+    const int nitems = g.nbx * g.nby * g.nbz;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int bx = item % g.nbx, by = (item / g.nbx) % g.nby, bz = item / (g.nbx * g.nby);
+        const int x0 = bx * TX3, y0 = by * TY3, z0 = bz * g.tz, z1 = min(z0 + g.tz, g.D + 1);
+        Stage3<T> st;
+        st.setup(g, x0, y0);
+        st.load(g, z0 - 1);
+        __syncthreads();   // the ring is free again
+        int prev = 0, cur = 1;
+        st.store(ring + prev * SPLANE3, bin, UL);
+        st.load(g, z0);
+        const int X = x0 + tx, Y = y0 + ty;
+        for (int Z = z0; Z < z1; Z++) {
+            st.store(ring + cur * SPLANE3, bin, UL);
+            if (Z + 1 < z1) st.load(g, Z + 1);
+            __syncthreads();
+            if (X <= g.W && Y <= g.H) {
+                const uint16_t *r0 = ring + prev * SPLANE3 + ty * SW3 + tx;
+                const uint16_t *r1 = ring + cur * SPLANE3 + ty * SW3 + tx;
+                uint32_t s[8];
+                s[0] = ((uint32_t)r0[0] << 3) | 0u;
+                s[1] = ((uint32_t)r0[1] << 3) | 1u;
+                s[2] = ((uint32_t)r0[SW3] << 3) | 2u;
+                s[3] = ((uint32_t)r0[SW3 + 1] << 3) | 3u;
+                s[4] = ((uint32_t)r1[0] << 3) | 4u;
+                s[5] = ((uint32_t)r1[1] << 3) | 5u;
+                s[6] = ((uint32_t)r1[SW3] << 3) | 6u;
+                s[7] = ((uint32_t)r1[SW3 + 1] << 3) | 7u;
+                // Batcher odd-even merge network, 19 comparators
+#define CS(a, b) { const uint32_t lo_ = min(s[a], s[b]), hi_ = max(s[a], s[b]); s[a] = lo_; s[b] = hi_; }
+                CS(0, 1) CS(2, 3) CS(4, 5) CS(6, 7) CS(0, 2) CS(1, 3) CS(4, 6) CS(5, 7) CS(1, 2) CS(5, 6)
+                CS(0, 4) CS(1, 5) CS(2, 6) CS(3, 7) CS(2, 4) CS(3, 5) CS(1, 2) CS(3, 4) CS(5, 6)
+#undef CS
+                walk_types<8, 3, kStride3, SMEM>(s, UL, tl, sh, ghist);
+            }
+            const int nxt = 3 - prev - cur;
+            prev = cur;
+            cur = nxt;
+        }
+    }
+    if (SMEM) flush_types<kTypes3, kStride3>(sh, ghist, L);
+}
+
+// Staging of the TX2+1 cells x0-1 .. x0+TX2-1 of a row (thread t: cells t
+// and, for thread 0, TX2), loaded one row ahead like Stage3.
+template <typename T>
+struct Stage2 {
+    int off[2];
+    bool ok[2];
+    T raw[2];
+    bool yin;
+
+    __device__ __forceinline__ void setup(const G2 &g, int x0)
+    {
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int i = threadIdx.x + q * kTmThreads;
+            const int gx = x0 - 1 + i;
+            ok[q] = i < SW2 && (unsigned)gx < (unsigned)g.W;
+            off[q] = ok[q] ? gx : 0;
+        }
+    }
+    __device__ __forceinline__ void load(const G2 &g, int y)
+    {
+        yin = y >= 0 && y < g.H;
+        const T *row = (const T *)g.f + (yin ? (int64_t)y * g.W : 0);
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+            if (ok[q] && yin) raw[q] = __ldg(row + off[q]);
+    }
+    __device__ __forceinline__ void store(uint16_t *slot, const TBin<T> &bin, uint32_t L) const
+    {
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int i = threadIdx.x + q * kTmThreads;
+            if (i < SW2) slot[i] = (uint16_t)((ok[q] && yin) ? bin(raw[q]) : L);
+        }
+    }
+};
+
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(kTmThreads, 2) k_types2(G2 g, const T *thr, int L, long long *ghist)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const size_t hb = SMEM ? (((size_t)L * kStride2 * 4 + 15) & ~(size_t)15) : 0;
+    int *sh = (int *)smem;
+    const size_t bb = tbin_smem_bytes<T>(L, thr != nullptr);
+    uint8_t *tl = smem + hb + bb;
+    uint16_t *ring = (uint16_t *)(smem + hb + bb + 16);
+    if (SMEM)
+        for (int i = threadIdx.x; i < L * kStride2; i += kTmThreads) sh[i] = 0;
+    for (int i = threadIdx.x; i < 16; i += kTmThreads) tl[i] = c_types2.t[i];
+    const TBin<T> bin = make_tbin<T>(thr, L, smem + hb);
+    __syncthreads();
+    const uint32_t UL = (uint32_t)L;
+    const int tx = threadIdx.x;
+    const int nitems = g.nbx * g.nby;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int bx = item % g.nbx, by = item / g.nbx;
+        const int x0 = bx * TX2, y0 = by * TY2, y1 = min(y0 + TY2, g.H + 1);
+        Stage2<T> st;
+        st.setup(g, x0);
+        st.load(g, y0 - 1);
+        __syncthreads();   // the ring is free again
+        int prev = 0, cur = 1;
+        st.store(ring + prev * SW2, bin, UL);
+        st.load(g, y0);
+        const int X = x0 + tx;
+        for (int Y = y0; Y < y1; Y++) {
+            st.store(ring + cur * SW2, bin, UL);
+            if (Y + 1 < y1) st.load(g, Y + 1);
+            __syncthreads();
+            if (X <= g.W) {
+                const uint16_t *r0 = ring + prev * SW2 + tx, *r1 = ring + cur * SW2 + tx;
+                uint32_t s[4] = {((uint32_t)r0[0] << 2) | 0u, ((uint32_t)r0[1] << 2) | 1u,
+                                 ((uint32_t)r1[0] << 2) | 2u, ((uint32_t)r1[1] << 2) | 3u};
+#define CS(a, b) { const uint32_t lo_ = min(s[a], s[b]), hi_ = max(s[a], s[b]); s[a] = lo_; s[b] = hi_; }
+                CS(0, 1) CS(2, 3) CS(0, 2) CS(1, 3) CS(1, 2)
+#undef CS
+                walk_types<4, 2, kStride2, SMEM>(s, UL, tl, sh, ghist);
+            }
+            const int nxt = 3 - prev - cur;
+            prev = cur;
+            cur = nxt;
+        }
+    }
+    if (SMEM) flush_types<kTypes2, kStride2>(sh, ghist, L);
+}
+
+template <typename KernelT>
+int grid_for(KernelT kernel, size_t smem, int num_sms, int64_t items, int grid_override, int *grid)
+{
+    EC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kTmThreads, smem));
+    if (occ < 1) { set_error("type-map kernel does not fit on an SM (%zu B shared)", smem); return EC_ERR_UNSUPPORTED; }
+    int64_t gr = grid_override > 0 ? grid_override : (int64_t)num_sms * occ;
+    if (gr > items) gr = items;
+    *grid = (int)(gr < 1 ? 1 : gr);
+    return EC_OK;
+}
+
+template <typename T>
+int launch_types(int ndim, const void *field, const int64_t *dims, const void *thr, int L, long long *hist,
+                 int tile_z, int grid_override, int num_sms, cudaStream_t s)
+{
+    const size_t bb = tbin_smem_bytes<T>(L, thr != nullptr);
+    int grid = 0, rc;
+    if (ndim == 3) {
+        G3 g;
+        g.f = field;
+        g.D = (int)dims[0]; g.H = (int)dims[1]; g.W = (int)dims[2];
+        g.tz = tile_z > 0 ? tile_z : 32;
+        g.nbx = (g.W + 1 + TX3 - 1) / TX3;
+        g.nby = (g.H + 1 + TY3 - 1) / TY3;
+        g.nbz = (g.D + 1 + g.tz - 1) / g.tz;
+        const int64_t items = (int64_t)g.nbx * g.nby * g.nbz;
+        if (items > INT32_MAX) { set_error("field too large for one launch"); return EC_ERR_UNSUPPORTED; }
+        const size_t hb = ((size_t)L * kStride3 * 4 + 15) & ~(size_t)15;
+        const size_t rest = bb + 256 + 3 * SPLANE3 * sizeof(uint16_t);
+        const T *t = (const T *)thr;
+        if (hb <= kTypeHistBudget) {
+            if ((rc = grid_for(k_types3<T, true>, hb + rest, num_sms, items, grid_override, &grid))) return rc;
+            k_types3<T, true><<<grid, kTmThreads, hb + rest, s>>>(g, t, L, hist);
+        } else {
+            if ((rc = grid_for(k_types3<T, false>, rest, num_sms, items, grid_override, &grid))) return rc;
+            k_types3<T, false><<<grid, kTmThreads, rest, s>>>(g, t, L, hist);
+        }
+    } else {
+        G2 g;
+        g.f = field;
+        g.H = (int)dims[0]; g.W = (int)dims[1];
+        g.nbx = (g.W + 1 + TX2 - 1) / TX2;
+        g.nby = (g.H + 1 + TY2 - 1) / TY2;
+        const int64_t items = (int64_t)g.nbx * g.nby;
+        if (items > INT32_MAX) { set_error("field too large for one launch"); return EC_ERR_UNSUPPORTED; }
+        const size_t hb = ((size_t)L * kStride2 * 4 + 15) & ~(size_t)15;
+        const size_t rest = bb + 16 + 3 * SW2 * sizeof(uint16_t);
+        const T *t = (const T *)thr;
+        if (hb <= kTypeHistBudget) {
+            if ((rc = grid_for(k_types2<T, true>, hb + rest, num_sms, items, grid_override, &grid))) return rc;
+            k_types2<T, true><<<grid, kTmThreads, hb + rest, s>>>(g, t, L, hist);
+        } else {
+            if ((rc = grid_for(k_types2<T, false>, rest, num_sms, items, grid_override, &grid))) return rc;
+            k_types2<T, false><<<grid, kTmThreads, rest, s>>>(g, t, L, hist);
+        }
+    }
+    EC_CUDA(cudaGetLastError());
+    return EC_OK;
+}
+
+int launch_type_map(int ndim, const void *field, const int64_t *dims, int dtype, const void *thr, int L,
+                    long long *hist, int tile_z, int grid, int num_sms, cudaStream_t s)
+{
+    switch (dtype) {
+    case EC_U8: return launch_types<uint8_t>(ndim, field, dims, thr, L, hist, tile_z, grid, num_sms, s);
+    case EC_U16: return launch_types<uint16_t>(ndim, field, dims, thr, L, hist, tile_z, grid, num_sms, s);
+    case EC_F32: return launch_types<float>(ndim, field, dims, thr, L, hist, tile_z, grid, num_sms, s);
+    }
+    set_error("unknown dtype %d", dtype);
+    return EC_ERR_DTYPE;
+}
+
 
 constexpr size_t kFlagBytes = 256;
 constexpr int kMaxWeightRows = 16;
@@ -133,10 +543,8 @@ int ec_type_map(ec_ctx *ctx, int32_t ndim, const void *field_dev, const int64_t 
     const int nt = ndim == 2 ? kTypes2 : kTypes3;
     long long nvert = 1;
     for (int i = 0; i < ndim; i++) {
-        if (dims[i] + 1 > (int64_t)1 << 40 || nvert > ((long long)1 << 62) / (dims[i] + 1)) {
-            set_error("field too large");
-            return EC_ERR_ARG;
-        }
+        // 32-bit cell coordinates in the kernels
+        if (dims[i] > ((int64_t)1 << 30)) { set_error("dims[%d] above 2^30", i); return EC_ERR_ARG; }
         nvert *= dims[i] + 1;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -155,9 +563,9 @@ int ec_type_map(ec_ctx *ctx, int32_t ndim, const void *field_dev, const int64_t 
         EC_CUDA(cudaStreamSynchronize(s));
         if (*ctx->host_flag) { set_error("thresholds are not non-decreasing"); return EC_ERR_ARG; }
     }
-    BinArgs ba{L, dtype, thresholds_dev};
     if (ctx->profile && (rc = prof_begin(ctx, s))) return rc;
-    rc = launch_type_map(ndim, field_dev, dims, ba, hist, ctx->tile_z, ctx->grid, ctx->num_sms, s);
+    rc = launch_type_map(ndim, field_dev, dims, dtype, thresholds_dev, L, hist, ctx->tile_z, ctx->grid,
+                         ctx->num_sms, s);
     if (rc) return rc;
     if (ctx->profile && (rc = prof_end(ctx, s))) return rc;
     k_type_scan<<<nt - 1, 1024, 0, s>>>(hist, L, counts_dev);

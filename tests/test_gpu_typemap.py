@@ -60,7 +60,7 @@ def rand_field(rng, shape, dtype, L):
     return f, thr
 
 
-# vertex tiles are 32 x 8 (x, y) and 32 planes deep in 3D, 256 wide and 64 rows in 2D
+# vertex tiles are 32 x 16 (x, y) and 32 planes deep in 3D, 512 wide and 64 rows in 2D
 SHAPES3 = [(1, 1, 1), (1, 1, 9), (2, 3, 5), (31, 7, 31), (32, 8, 32), (33, 9, 40), (40, 17, 66), (5, 70, 3)]
 SHAPES2 = [(1, 1), (1, 300), (63, 255), (64, 256), (130, 520), (300, 7)]
 
@@ -85,7 +85,7 @@ def test_random_2d(ctx, shape, dtype):
 
 @pytest.mark.parametrize("L", [1, 2, 255, 1024])
 def test_level_counts_3d_shared_histogram(ctx, L):
-    """Up to the shared-memory budget (22 types x 1117 levels) the block
+    """Up to the shared-memory budget (rows of 23 int32 x 1113 levels) the block
     histograms live in shared memory."""
     rng = np.random.default_rng(L)
     f = rng.random((20, 11, 37)).astype(np.float32)
