@@ -6,11 +6,13 @@ histogram kernel over every voxel, the scan.  Inputs are resident in HBM
 before the timed region (537 MB, larger than L2, so no flush is needed
 between steps).  Prints one JSON line, which also carries the same step with
 all four descriptors, the end-to-end number through the host-buffer call,
+the contribution-type map of the same field (22 vertex types x 1024 levels)
 and the batched-versus-per-field comparison on the served request mix.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-  python bench.py --profile-case     (the kernel alone on a 256 x 512 x 512
-                                      slab of the field, for ncu captures)
+  python bench.py --profile-case [typemap]   (the curve kernel, or the type
+                                      map, alone on a 256 x 512 x 512 slab of
+                                      the field, for ncu captures)
 
 --impl reference times the CPU oracle (the plain cell-counting reference) on
 this machine's host cores, on a bounded sample of the same workload.
@@ -49,12 +51,16 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_voxel3d_fast_512cube_f32.jso
 # Files that define the profiled kernel (k_voxel3d_fast and what it inlines):
 # the stored ncu traffic is used only while they are unchanged.
 KERNEL_SOURCES = ("ec_fast3d.cu", "ec_fast3d.cuh", "ec_swar.h", "ec_rules.h", "ec_internal.h")
+# The contribution-type map's histogram kernel (k_types3) and its summary.
+TYPEMAP_KERNEL = "k_types3"
+TYPEMAP_SOURCES = ("ec_typemap.cu", "ec_fast3d.cuh", "ec_rules.h", "ec_internal.h")
+TYPEMAP_SUMMARY = os.path.join(ROOT, "profiles", "k_types3_512cube_f32.json")
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2311_11740_gb300", "csrc")
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -122,14 +128,14 @@ class ClockSampler:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
-def traffic_per_launch():
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, or None when the kernel sources changed since the capture."""
-    if not os.path.exists(PROFILE_SUMMARY):
+def traffic_per_launch(summary=PROFILE_SUMMARY, sources=KERNEL_SOURCES):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, or
+    None when the kernel's sources changed since the capture."""
+    if not os.path.exists(summary):
         return None
-    with open(PROFILE_SUMMARY) as f:
+    with open(summary) as f:
         d = json.load(f)
-    if d.get("kernel_source_hash") != kernel_source_hash():
+    if d.get("kernel_source_hash") != kernel_source_hash(sources):
         return None
     return d.get("dram_bytes_per_full_launch")
 
@@ -233,6 +239,68 @@ def batched_vs_per_field(ec, ctx, n_requests, seed=5):
                        "host_fields": "page-locked"}}
 
 
+def type_map_section(ec, ctx, field, thr, steps, with_cpu, budget_s):
+    """The contribution-type map of the same field (ec_type_map: the 22
+    Table 2 types at each of the 1024 levels), timed per call; the library's
+    Table 2 weights applied to it (ec_apply_weights) must give the curve
+    request's EC, perimeter, area and volume curves.  The CPU leg times the
+    oracle (the definition, level by level) on one level pass over a
+    bounded sample and scales it to all L levels."""
+    import numpy as np
+    import torch
+    nt = ec.NTYPES[3]
+    counts = torch.empty((nt, L), dtype=torch.int64, device="cuda")
+    ec.type_map(field, thr, out=counts, ctx=ctx)
+    # weights per type from the library's per-mask table: any mask of the type
+    tt, vt = ec.type_table(3), ec.vertex_table_3d()
+    W = np.stack([vt[int(np.flatnonzero(tt == t)[0])] for t in range(nt)], axis=1).astype(np.int32)
+    curves = ec.apply_weights(counts, W, [8, 2, 4, 8], ctx=ctx)
+    same = torch.equal(curves, ec.curve(field, thr, descriptors=DESC_ALL, ctx=ctx))
+    torch.cuda.synchronize()
+    ctx.profile_read()
+    ms = time_device(lambda: ec.type_map(field, thr, out=counts, ctx=ctx), steps)
+    kms, kl = ctx.profile_read()
+    kus = kms / max(kl, 1) * 1e3
+    wus = time_device(lambda: ec.apply_weights(counts, W, [8, 2, 4, 8], out=curves, ctx=ctx), steps) * 1e3
+    peak, peak_kind = measured_peaks()
+    vox = field.numel()
+    out = {"workload": "the same 512^3 float32 field and 1024 thresholds; counts of the 22 Table 2 vertex types "
+                       "at every level (int64 [22][1024]) over the 513^3 vertices",
+           "ms_per_step": ms, "value": vox / ms / 1e6, "unit": "Gvoxels/s",
+           "per_step": "ec_type_map: memset + k_types3 + k_type_scan + k_type_empty",
+           "gpu_launches_per_step": 3,
+           "roofline": {"bound": "hbm", "kernel": TYPEMAP_KERNEL, "achieved": vox * 4 / (kus * 1e-6) / 1e9,
+                        "peak": peak, "unit": "GB/s", "frac": vox * 4 / (kus * 1e-6) / 1e9 / peak,
+                        "peak_source": peak_kind,
+                        "traffic": traffic_per_launch(TYPEMAP_SUMMARY, TYPEMAP_SOURCES),
+                        "kernel_avg_us": kus, "algorithmic_bytes_per_launch": vox * 4},
+           "apply_weights_us": wus, "weighted_equals_curves": bool(same)}
+    if with_cpu:
+        from oracle import typemap as tm
+        import oracle
+        f_cpu, t_np = field.cpu(), thr.cpu().numpy()
+        planes = 8
+        t0 = time.perf_counter()
+        tm.type_counts_at(oracle.bin_field(np.ascontiguousarray(f_cpu[:planes].numpy()), t_np, L), L, L // 2)
+        per_plane = (time.perf_counter() - t0) / planes
+        planes = int(max(8, min(field.shape[0], budget_s / 3 / max(per_plane, 1e-6))))
+        sample = np.ascontiguousarray(f_cpu[:planes].numpy())
+        t0 = time.perf_counter()
+        bins = oracle.bin_field(sample, t_np, L)
+        t_bin = time.perf_counter() - t0
+        ks = (0, L // 2, L - 1)
+        t0 = time.perf_counter()
+        for k in ks:
+            tm.type_counts_at(bins, L, k)
+        t_level = (time.perf_counter() - t0) / len(ks)
+        est = t_bin + L * t_level
+        out["cpu_baseline"] = {"value": sample.size / est / 1e9, "unit": "Gvoxels/s", "cores": 1, "kind": "oracle",
+                               "sample": f"oracle binning + 3 of the 1024 level passes over the first {planes} "
+                                         f"z-planes ({sample.size} voxels), scaled to 1024 levels "
+                                         f"({t_bin:.2f} s + 1024 x {t_level:.3f} s)"}
+    return out
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle timed per step on a bounded sample."""
     import numpy as np
@@ -282,8 +350,9 @@ def main():
     ap.add_argument("--small", type=int, default=0, help="testing only: edge of a smaller cube")
     ap.add_argument("--batch-requests", type=int, default=256)
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--profile-case", action="store_true",
-                    help="run two curve requests on the first 256 planes of the field and exit")
+    ap.add_argument("--no-type-map", action="store_true")
+    ap.add_argument("--profile-case", nargs="?", const="curve", choices=("curve", "typemap"),
+                    help="run two curve requests (or two type maps) on the first 256 planes of the field and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -306,6 +375,13 @@ def main():
     if args.profile_case:
         slab = field[:256].contiguous()
         ctx = ec.Context(local)
+        if args.profile_case == "typemap":
+            for _ in range(2):
+                res = ec.type_map(slab, thr, ctx=ctx)
+            torch.cuda.synchronize()
+            print(json.dumps({"profile_case": "256x512x512 float32 slab of the benchmark field, type map",
+                              "full_vertices_at_top": int(res[21, -1])}))
+            return 0
         for _ in range(2):
             res = ec.curve(slab, thr, descriptors=DESC, ctx=ctx)
         torch.cuda.synchronize()
@@ -366,6 +442,8 @@ def main():
     ec.curve(field, thr, descriptors=DESC_ALL, out=out_all, ctx=ctx)
     all_ms = time_device(lambda: ec.curve(field, thr, descriptors=DESC_ALL, out=out_all, ctx=ctx), 50)
     ctx.profile_read()
+    type_map = None if (args.no_type_map or rank != 0) else type_map_section(
+        ec, ctx, field, thr, 20, not args.no_cpu_baseline, args.cpu_budget)
     batched = None if (args.no_batch or rank != 0) else batched_vs_per_field(ec, ctx, args.batch_requests)
 
     if rank != 0:
@@ -390,6 +468,7 @@ def main():
         "clocks": clocks,
         "all_descriptors": {"descriptors": "EC+perimeter+area+volume", "ms_per_step": all_ms,
                             "value": vox / all_ms / 1e6, "unit": "Gvoxels/s"},
+        "type_map": type_map,
         "batched_vs_per_field": batched,
     }
     if not args.no_cpu_baseline:
