@@ -53,7 +53,7 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_voxel3d_fast_512cube_f32.jso
 KERNEL_SOURCES = ("ec_fast3d.cu", "ec_fast3d.cuh", "ec_swar.h", "ec_rules.h", "ec_internal.h")
 # The contribution-type map's histogram kernel (k_types3) and its summary.
 TYPEMAP_KERNEL = "k_types3"
-TYPEMAP_SOURCES = ("ec_typemap.cu", "ec_fast3d.cuh", "ec_rules.h", "ec_internal.h")
+TYPEMAP_SOURCES = ("ec_typemap.cu", "ec_types.h", "ec_fast3d.cuh", "ec_rules.h", "ec_internal.h")
 TYPEMAP_SUMMARY = os.path.join(ROOT, "profiles", "k_types3_512cube_f32.json")
 
 

@@ -13,6 +13,7 @@
 
 #include "ec_internal.h"
 #include "ec_rules.h"
+#include "ec_types.h"
 #include "ec_swar.h"
 
 namespace ec {

@@ -16,6 +16,7 @@
 #include "ec_fast3d.cuh"   // fbin / IBin: level of a value (uniform-spacing guess, binary-search fallback)
 #include "ec_internal.h"
 #include "ec_rules.h"
+#include "ec_types.h"
 
 using namespace ec;
 
