@@ -255,6 +255,23 @@ int ec_server_wait_all(ec_server *server, int64_t timeout_ms);
 int ec_server_reset_stats(ec_server *server);
 int ec_server_destroy(ec_server *server);
 
+/* Low-memory 3D processing straight from a raw file (Algorithm 1 reads a raw
+ * data file; Sec. 2.3 reads from it only what is needed): the field is the
+ * d*h*w values of `dtype` (native byte order, x fastest) stored contiguously
+ * from byte `offset` of the file at `path`.  Runs ec_curve_3d_stream with a
+ * producer that reads each slab's planes (with its halo planes) by pread into
+ * one of two page-locked staging buffers of (min(slab_planes, d) + 2) planes,
+ * allocated for the call, and copies them to the device on the streaming
+ * side stream; the host reads the next slab while the GPU counts this one.
+ * Slabs of 4 MiB or more are read by up to 8 threads.  Other arguments and
+ * the result (written to out_host before return) are those of
+ * ec_curve_3d_stream.  Errors: EC_ERR_ARG if the file cannot be opened, is
+ * shorter than offset + d*h*w*sizeof(dtype), or a read fails (the message
+ * names the plane); EC_ERR_OOM if the staging cannot be allocated. */
+int ec_curve_3d_file(ec_ctx *ctx, const char *path, int64_t offset, const int64_t dims[3], int dtype,
+                     const void *thresholds_host, int32_t L, int connectivity, uint32_t descriptors,
+                     int64_t slab_planes, size_t device_mem_cap, int64_t *out_host);
+
 /* ----------------------------------------------- contribution-type map
  * The paper's full output (Sec. 2, Algorithm 1 and Table 1; Sec. 2.2,
  * Algorithm 3 and Table 2; Sec. 4): how many grid vertices have each

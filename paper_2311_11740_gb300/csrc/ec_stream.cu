@@ -17,10 +17,16 @@
 // previous buffer, so every plane crosses the host link once.  The memory
 // cap bounds the number and height of the buffers.
 #include <cuda_runtime.h>
+#include <errno.h>
+#include <fcntl.h>
 #include <stdint.h>
 #include <string.h>
+#include <sys/stat.h>
+#include <unistd.h>
 
 #include <algorithm>
+#include <thread>
+#include <vector>
 
 #include "ec_internal.h"
 
@@ -193,3 +199,144 @@ extern "C" int ec_curve_3d_stream(ec_ctx *ctx, const void *host_field, ec_slab_f
     if (hflags[0] & 4) { set_error("a bounded device wait gave up"); return EC_ERR_TIMEOUT; }
     return EC_OK;
 }
+
+// ------------------------------------------------------------ raw files
+//
+// Algorithm 1 starts from a raw data file and the low-memory mode of
+// Sec. 2.3 reads only what a vertex needs from it.  ec_curve_3d_file streams
+// z-slabs straight from such a file: the streaming path above asks for the
+// planes of each slab (with its halo planes), the producer below reads them
+// with pread into one of two page-locked staging buffers and enqueues their
+// copy to the device on the side stream.  A staging buffer is reused only
+// after the copy that last read it has finished (an event per buffer), so
+// the host reads slab i+1 while the GPU counts slab i.
+
+namespace {
+
+struct FileSlabs {
+    int fd = -1;
+    int64_t offset = 0, d = 0;
+    size_t plane = 0, cap = 0;          // bytes per plane, bytes per staging buffer
+    void *pinned[2] = {nullptr, nullptr};
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    int next = 0;
+    int64_t bad_plane = -1;             // first plane whose read failed
+    int bad_errno = 0;
+    ~FileSlabs()
+    {
+        for (int i = 0; i < 2; i++) {
+            if (copied[i]) { cudaEventSynchronize(copied[i]); cudaEventDestroy(copied[i]); }
+            if (pinned[i]) cudaFreeHost(pinned[i]);
+        }
+        if (fd >= 0) close(fd);
+    }
+};
+
+int file_producer(void *user, int64_t z0, int64_t z1, void *dst_dev, void *stream)
+{
+    FileSlabs &f = *(FileSlabs *)user;
+    const int64_t a = std::max<int64_t>(z0, 0), b = std::min<int64_t>(z1, f.d);   // halo planes outside are ignored
+    if (b <= a) return 0;
+    const size_t bytes = (size_t)(b - a) * f.plane;
+    if (bytes > f.cap) return 1;
+    const int i = f.next;
+    f.next ^= 1;
+    if (cudaEventSynchronize(f.copied[i]) != cudaSuccess) return 2;
+    // large slabs are read by several threads in plane-aligned chunks
+    const int64_t nplanes = b - a;
+    const int nthr = (int)std::max<int64_t>(1, std::min<int64_t>({8, nplanes, (int64_t)(bytes >> 22)}));
+    std::vector<int64_t> bad(nthr, -1);
+    std::vector<int> bad_err(nthr, 0);
+    auto read_part = [&](int t) {
+        const int64_t p0 = nplanes * t / nthr, p1 = nplanes * (t + 1) / nthr;
+        char *p = (char *)f.pinned[i] + (size_t)p0 * f.plane;
+        off_t off = (off_t)(f.offset + (a + p0) * (int64_t)f.plane);
+        size_t left = (size_t)(p1 - p0) * f.plane;
+        const size_t total = left;
+        while (left > 0) {
+            const ssize_t r = pread(f.fd, p, left, off);
+            if (r < 0 && errno == EINTR) continue;
+            if (r <= 0) {
+                bad[t] = a + p0 + (int64_t)((total - left) / f.plane);
+                bad_err[t] = r < 0 ? errno : 0;
+                return;
+            }
+            p += r;
+            off += r;
+            left -= (size_t)r;
+        }
+    };
+    if (nthr == 1) {
+        read_part(0);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 1; t < nthr; t++) th.emplace_back(read_part, t);
+        read_part(0);
+        for (auto &x : th) x.join();
+    }
+    for (int t = 0; t < nthr; t++)
+        if (bad[t] >= 0) {
+            f.bad_plane = bad[t];
+            f.bad_errno = bad_err[t];
+            return 3;
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync((char *)dst_dev + (size_t)(a - z0) * f.plane, f.pinned[i], bytes, cudaMemcpyHostToDevice,
+                        s) != cudaSuccess)
+        return 4;
+    if (cudaEventRecord(f.copied[i], s) != cudaSuccess) return 5;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int ec_curve_3d_file(ec_ctx *ctx, const char *path, int64_t offset, const int64_t dims[3], int dtype,
+                                const void *thresholds_host, int32_t L, int connectivity, uint32_t descriptors,
+                                int64_t slab_planes, size_t device_mem_cap, int64_t *out_host)
+{
+    clear_error();
+    if (!ctx) { set_error("ctx is NULL"); return EC_ERR_ARG; }
+    if (!path) { set_error("path is NULL"); return EC_ERR_ARG; }
+    int rc = validate_request(3, path, dims, dtype, thresholds_host, L, connectivity, descriptors, out_host);
+    if (rc) return rc;
+    if (offset < 0) { set_error("offset < 0"); return EC_ERR_ARG; }
+    if (slab_planes < 1) { set_error("slab_planes must be >= 1"); return EC_ERR_ARG; }
+    if (L == 0) return EC_OK;
+    FileSlabs f;
+    f.fd = open(path, O_RDONLY);
+    if (f.fd < 0) { set_error("cannot open %s: %s", path, strerror(errno)); return EC_ERR_ARG; }
+    struct stat st;
+    if (fstat(f.fd, &st) != 0) { set_error("cannot stat %s: %s", path, strerror(errno)); return EC_ERR_ARG; }
+    f.offset = offset;
+    f.d = dims[0];
+    f.plane = (size_t)dims[1] * (size_t)dims[2] * (size_t)dtype_size(dtype);
+    const int64_t need = offset + (int64_t)f.plane * dims[0];
+    if ((int64_t)st.st_size < need) {
+        set_error("%s holds %lld bytes, the field needs %lld from offset %lld", path, (long long)st.st_size,
+                  (long long)need, (long long)offset);
+        return EC_ERR_ARG;
+    }
+    // a slab asks for at most min(slab_planes, d) + 2 planes (halo planes outside the file are not read)
+    f.cap = (size_t)(std::min<int64_t>(slab_planes, dims[0]) + 2) * f.plane;
+    {
+        DeviceGuard dg(ctx->device);
+        for (int i = 0; i < 2; i++) {
+            if (cudaMallocHost(&f.pinned[i], f.cap) != cudaSuccess) {
+                cudaGetLastError();
+                f.pinned[i] = nullptr;
+                set_error("cannot allocate %zu bytes of page-locked staging", f.cap);
+                return EC_ERR_OOM;
+            }
+            EC_CUDA(cudaEventCreateWithFlags(&f.copied[i], cudaEventDisableTiming));
+        }
+    }
+    rc = ec_curve_3d_stream(ctx, nullptr, file_producer, &f, dims, dtype, thresholds_host, L, connectivity,
+                            descriptors, slab_planes, device_mem_cap, out_host);
+    if (rc && f.bad_plane >= 0) {
+        set_error("reading plane %lld of %s failed: %s", (long long)f.bad_plane, path,
+                  f.bad_errno ? strerror(f.bad_errno) : "end of file");
+        return EC_ERR_ARG;
+    }
+    return rc;
+}
+

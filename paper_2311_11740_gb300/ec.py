@@ -84,6 +84,8 @@ def lib():
             L.ec_type_map.argtypes = [P, I32, P, ctypes.POINTER(I64), ctypes.c_int, P, I32, P, P]
             L.ec_apply_weights.argtypes = [P, I32, P, I32, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), P, P]
             L.ec_type_table.argtypes = [I32, P]
+            L.ec_curve_3d_file.argtypes = [P, ctypes.c_char_p, I64, ctypes.POINTER(I64), ctypes.c_int, P, I32,
+                                           ctypes.c_int, U32, I64, ctypes.c_size_t, P]
             _lib = L
     return _lib
 
@@ -396,6 +398,29 @@ def hashbox_stream(spec: HashboxSpec, nz: int, thresholds=None, L=4096, descript
     _check(lib().ec_curve_3d_stream(ctx.handle, None, cb, ctypes.c_void_p(user), _dims(dims), EC_U16,
                                     ctypes.c_void_p(thr_ptr), int(L), 26, int(descriptors), int(slab_planes),
                                     ctypes.c_size_t(int(device_mem_cap)), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def curve_3d_file(path, dims, dtype, thresholds=None, L=None, offset=0, connectivity=26,
+                  descriptors=EC_DESC_EC, slab_planes=64, device_mem_cap=0, ctx: Context | None = None,
+                  device: int = 0):
+    """Curves of a 3D field stored raw in a file (ec_curve_3d_file).  dims =
+    (d, h, w); dtype an ec dtype code or numpy dtype; thresholds a host array
+    (or None for identity levels with L).  Returns int64 numpy [rows, L]."""
+    ctx = ctx or default_context(device)
+    code = dtype if isinstance(dtype, int) else {np.dtype(np.uint8): EC_U8, np.dtype(np.uint16): EC_U16,
+                                                  np.dtype(np.float32): EC_F32}[np.dtype(dtype)]
+    thr = None
+    if thresholds is not None:
+        thr = np.ascontiguousarray(np.asarray(thresholds, dtype=_NP_DTYPES[code]))
+        L = thr.size if L is None else L
+    if L is None:
+        raise ValueError("L is required with identity levels")
+    out = np.zeros((n_rows(descriptors), L), dtype=np.int64)
+    _check(lib().ec_curve_3d_file(ctx.handle, os.fsencode(path), int(offset), _dims(dims), code,
+                                  None if thr is None else thr.ctypes.data_as(ctypes.c_void_p), int(L),
+                                  int(connectivity), int(descriptors), int(slab_planes),
+                                  ctypes.c_size_t(int(device_mem_cap)), out.ctypes.data_as(ctypes.c_void_p)))
     return out
 
 
