@@ -369,7 +369,7 @@ def realtime_frames_section(ec, ctx, nframes=300, seed=7):
                             "EC+perimeter+area, page-locked host tiles through ec_server, one frame in flight",
                 "frames": nframes, "p50_us": us[len(us) // 2], "p99_us": us[min(len(us) - 1, int(0.99 * len(us)))],
                 "frames_per_s": 1.0 / mean, "mpixels_s": px / mean / 1e6, "needed_mpixels_s_at_30fps": px * 30 / 1e6,
-                "oracle_ms_per_frame_1_thread_per_tile": oracle_ms, "identical": bool(ok)}
+                "oracle_ms_per_frame": oracle_ms, "oracle_cores": oracle.num_threads(), "identical": bool(ok)}
     except Exception as e:   # the optional leg must not cost the line
         return {"error": f"{type(e).__name__}: {e}"}
 
