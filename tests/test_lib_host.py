@@ -91,3 +91,17 @@ def test_type_table_rows_carry_the_paper_weights(libec):
     for m in range(256):
         r = rows[int(tt[m])]
         assert Fraction(int(vt[m, 0]), 8) == r["EC"] and Fraction(int(vt[m, 3]), 8) == r["Volume"], m
+
+
+def test_bench_type_weights_are_table2_columns(libec):
+    """bench.py weights the type map with the library's per-mask table taken
+    at one mask of each type; those weights are Table 2's columns (8 EC, 2
+    perimeter, 4 area with the row-10 erratum, 8 volume) in row order."""
+    from paper_2311_11740_gb300 import ec
+    tt, vt = ec.type_table(3), ec.vertex_table_3d()
+    W = np.stack([vt[int(np.flatnonzero(tt == t)[0])] for t in range(22)], axis=1)
+    _, by_class = _tables.table2()
+    rows = sorted(by_class.values(), key=lambda r: r["row"])
+    want = np.array([[int(8 * r["EC"]) for r in rows], [int(2 * r["Perim"]) for r in rows],
+                     [int(4 * r["AreaUsed"]) for r in rows], [int(8 * r["Volume"]) for r in rows]])
+    np.testing.assert_array_equal(W, want)
