@@ -225,3 +225,31 @@ def test_apply_weights_rejects_a_non_multiple():
     assert tm.apply_weights(counts, [[2, 4]], [2]).tolist() == [[7, 10]]
     with pytest.raises(ValueError):
         tm.apply_weights(counts, [[1, 0]], [2])
+
+
+def test_worked_example_of_sec2_vertex_contribution():
+    """The single-vertex walk-through of Sec. 2 (tests/golden fixture): the
+    central vertex is born as one-face at 0, turns two-face diagonal at 1,
+    then three-face, then full; the other 8 vertices of the 3 x 3 grid touch
+    one or two pixels each."""
+    import os
+    rows, want = [], {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sec2_vertex_contribution_example.txt")
+    for line in open(path):
+        p = line.split()
+        if not p or p[0].startswith("#"):
+            continue
+        if p[0] == "field":
+            rows.append([int(v) for v in p[1:]])
+        elif p[0] == "level":
+            want[int(p[1])] = T1_ORDER.index(p[2])
+    bins = np.array(rows, np.int32)
+    counts = tm.type_map(bins, 4)
+    center_mask = {k: sum(1 << (dx + 2 * dy) for dy in (0, 1) for dx in (0, 1) if bins[dy, dx] <= k) for k in range(4)}
+    tab = tm.type_table(2)
+    for k, t in want.items():
+        assert tab[center_mask[k]] == t, k
+    # the whole 3 x 3 vertex grid at the first two levels (the 8 outer vertices see 1 or 2 pixels)
+    assert counts[:, 0].tolist() == [5, 4, 0, 0, 0, 0]
+    assert counts[:, 1].tolist() == [2, 6, 0, 1, 0, 0]
+    assert counts[:, 3].tolist() == [0, 4, 4, 0, 0, 1]
