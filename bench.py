@@ -46,14 +46,14 @@ N = 512
 L = 1024
 DESC = 13            # EC | AREA | VOLUME
 DESC_ALL = 15        # EC | PERIMETER | AREA | VOLUME
-KERNEL = "k_voxel3d_fast"
+KERNEL = "k_planar3d"
 LAUNCHES_PER_STEP = 3   # spacing check, histogram kernel, scan
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_voxel3d_fast_512cube_f32.json")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_planar3d_512cube_f32.json")
 
 
-# Files that define the profiled kernel (k_voxel3d_fast and what it inlines):
+# Files that define the profiled kernel (k_planar3d and what it inlines):
 # the stored ncu traffic is used only while they are unchanged.
-KERNEL_SOURCES = ("ec_fast3d.cu", "ec_fast3d.cuh", "ec_swar.h", "ec_rules.h", "ec_internal.h")
+KERNEL_SOURCES = ("ec_planar3d.cu", "ec_slice.h", "ec_fast3d.cuh", "ec_swar.h", "ec_rules.h", "ec_internal.h")
 # The contribution-type map's histogram kernel (k_types3) and its summary.
 TYPEMAP_KERNEL = "k_types3"
 TYPEMAP_SOURCES = ("ec_typemap.cu", "ec_types.h", "ec_fast3d.cuh", "ec_rules.h", "ec_internal.h")
@@ -567,7 +567,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if not args.small else f"{n}^3 test cube", "field_bytes": vox * 4,
                    "l2": "inputs larger than L2 (537 MB field), no flush",
-                   "per_step": "ec_curve_3d: memset + k_uniform_check + k_voxel3d_fast + k_scan"},
+                   "per_step": "ec_curve_3d: memset + k_uniform_check + k_planar3d + k_scan"},
         "roofline": {"bound": "hbm", "kernel": KERNEL, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
                      "kernel_avg_us": kernel_avg_s * 1e6, "algorithmic_bytes_per_launch": bytes_per_launch},

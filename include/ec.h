@@ -155,7 +155,15 @@ int ec_curve_3d(ec_ctx *ctx, const void *field_dev, const int64_t dims[3], int d
  *    overlaps on the GPU (other streams or host threads) race on it and give
  *    wrong curves, so serialise them.
  *  - The first call on a device looks up the array's address with that
- *    device current; make it before any stream capture.                    */
+ *    device current.  Under CUDA's lazy module loading this lookup loads the
+ *    library's device code on that device and reserves the array, so the
+ *    first call may allocate and synchronise implicitly: make one warm-up
+ *    call per device outside the latency-critical loop and before any stream
+ *    capture.  Later calls allocate nothing.
+ *  - The call does not synchronise, so failures on the device are not
+ *    turned into a status: when a bounded device wait gives up, every entry
+ *    of the affected curve rows reads INT64_MIN (a value no curve can take);
+ *    check for it if you need to tell such a failure from a real curve.    */
 int ec_curve_3d_noalloc(const void *field_dev, const int64_t dims[3], int dtype, const void *thresholds_dev,
                         int32_t L, int connectivity, uint32_t descriptors, int64_t *out_dev, void *stream);
 

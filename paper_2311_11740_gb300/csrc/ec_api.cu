@@ -14,6 +14,7 @@
 #include "ec_internal.h"
 #include "ec_rules.h"
 #include "ec_types.h"
+#include "ec_slice.h"
 #include "ec_swar.h"
 
 namespace ec {
@@ -46,6 +47,115 @@ using namespace ec;
 namespace {
 
 constexpr size_t kFlagBytes = 256;
+
+// The planar per-voxel form (ec_slice.h) on random small grids with many tied
+// levels, walked the way the kernels walk a column (one quad of four voxels
+// along x, or two stacked quads; start state from the plane below the first,
+// planes outside the field never active), summed per level and compared with the vertex tables
+// summed over every vertex of the grid (8 EC, 2 perimeter, 4 area, 8 volume).
+// Returns the number of mismatching (trial, level, descriptor) entries.
+int64_t selfcheck_planar(const Table3D &t3)
+{
+    uint64_t rs = 0xD1B54A32D192ED03ull;
+    auto rnd = [&rs]() {
+        rs ^= rs << 13; rs ^= rs >> 7; rs ^= rs << 17;
+        return rs;
+    };
+    int64_t bad = 0;
+    for (int trial = 0; trial < 3000; trial++) {
+        const int D = 1 + (int)(rnd() % 5), H = 1 + (int)(rnd() % 5), W = 1 + (int)(rnd() % 10);
+        const int L = trial % 4 == 0 ? 2 : (trial % 4 == 1 ? 4 : (trial % 4 == 2 ? 9 : 300));
+        // level of every voxel; L (never active) outside the field
+        std::vector<int> lev((size_t)D * H * W);
+        for (auto &v : lev) v = (int)(rnd() % (uint64_t)(L + 1));
+        auto key = [&](int z, int y, int x) -> uint32_t {
+            if (z < 0 || z >= D || y < 0 || y >= H || x < 0 || x >= W) return (uint32_t)L;
+            return (uint32_t)lev[((size_t)z * H + y) * W + x];
+        };
+        auto pair = [&](int z, int y, int x) { return key(z, y, x) | (key(z, y, x + 1) << 16); };
+        auto row5 = [&](int z, int y, int x) {
+            return Row5{pair(z, y, x - 1), pair(z, y, x), pair(z, y, x + 1), pair(z, y, x + 2), pair(z, y, x + 3)};
+        };
+        std::vector<int64_t> h((size_t)(L + 1) * 4, 0);
+        std::vector<int64_t> h2((size_t)(L + 1) * 4, 0);
+        // the two-row form (stacked quads, area as free faces)
+        for (int y = 0; y < H; y += 2)
+            for (int x = 0; x < W; x += 4) {
+                Row5 P[4], Q[4];
+                for (int r = 0; r < 4; r++) {
+                    P[r] = row5(-1, y - 1 + r, x);
+                    Q[r] = row5(0, y - 1 + r, x);
+                }
+                SliceState sa{}, sb{};
+                slice_pair_begin<true>(P, Q, sa, sb);
+                for (int z = 0; z < D; z++) {
+                    for (int r = 0; r < 4; r++) {
+                        P[r] = Q[r];
+                        Q[r] = row5(z + 1, y - 1 + r, x);
+                    }
+                    SliceOut oa, ob;
+                    slice_pair<AREA_FREE_FACES, true>(P, Q, sa, sb, oa, ob);
+                    for (int half = 0; half < 2; half++) {
+                        const SliceOut &o = half ? ob : oa;
+                        for (int v = 0; v < 4; v++) {
+                            const uint32_t k = key(z, y + half, x + v);
+                            const int sh = 8 * v;
+                            h2[k * 4 + 0] += (int8_t)(uint8_t)(o.ec >> sh);
+                            h2[k * 4 + 1] += (int8_t)(uint8_t)(o.per >> sh);
+                            h2[k * 4 + 2] += 2 * (int)((o.area >> sh) & 0xFFu) - 6;
+                            h2[k * 4 + 3] += 1;
+                        }
+                    }
+                }
+            }
+        for (int y = 0; y < H; y++)
+            for (int x = 0; x < W; x += 4) {
+                Row5 P[3], Q[3];
+                for (int dy = 0; dy < 3; dy++) {
+                    P[dy] = row5(-1, y - 1 + dy, x);
+                    Q[dy] = row5(0, y - 1 + dy, x);
+                }
+                SliceState st{};
+                slice_begin<true>(P, Q, st);
+                for (int z = 0; z < D; z++) {
+                    for (int dy = 0; dy < 3; dy++) {
+                        P[dy] = Q[dy];
+                        Q[dy] = row5(z + 1, y - 1 + dy, x);
+                    }
+                    const SliceOut o = slice_quad<true, true>(P, Q, st);
+                    for (int v = 0; v < 4; v++) {
+                        const uint32_t k = key(z, y, x + v);
+                        const int sh = 8 * v;
+                        h[k * 4 + 0] += (int8_t)(uint8_t)(o.ec >> sh);
+                        h[k * 4 + 1] += (int8_t)(uint8_t)(o.per >> sh);
+                        h[k * 4 + 2] += (int8_t)(uint8_t)(o.area >> sh);
+                        h[k * 4 + 3] += 1;
+                    }
+                }
+            }
+        int64_t run[4] = {0, 0, 0, 0}, run2[4] = {0, 0, 0, 0};
+        for (int k = 0; k < L; k++) {
+            int64_t want[4] = {0, 0, 0, 0};
+            for (int z = 0; z <= D; z++)
+                for (int y = 0; y <= H; y++)
+                    for (int x = 0; x <= W; x++) {
+                        unsigned m = 0;
+                        for (unsigned b = 0; b < 8; b++)
+                            if ((int)key(z - 1 + (int)(b >> 2), y - 1 + (int)((b >> 1) & 1), x - 1 + (int)(b & 1)) <= k)
+                                m |= 1u << b;
+                        for (int d = 0; d < 4; d++) want[d] += t3.v[m][d];
+                    }
+            const int scale[4] = {8, 2, 4, 8};
+            for (int d = 0; d < 4; d++) {
+                run[d] += h[(size_t)k * 4 + d];
+                run2[d] += h2[(size_t)k * 4 + d];
+                bad += run[d] * scale[d] != want[d];
+                bad += run2[d] * scale[d] != want[d];
+            }
+        }
+    }
+    return bad;
+}
 
 }  // namespace
 
@@ -167,6 +277,7 @@ int ec::enqueue_curve(const CurvePlan &plan, int ndim, const void *field, const 
     const int algo = plan.algo == ALGO_VERTEX ? ALGO_VERTEX : ALGO_VOXEL;
     BinArgs ba{L, dtype, thr};
     HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0, plan.hist_schedule};
+    ha.planar = plan.algo == ALGO_AUTO || plan.algo == ALGO_PLANAR;
     int rc;
     if (plan.prof && (rc = prof_begin(plan.prof, s))) return rc;
     if (ndim == 3) {
@@ -276,7 +387,7 @@ int ec_ctx_set_option(ec_ctx *ctx, int option, int64_t value)
     if (!ctx) { set_error("ctx is NULL"); return EC_ERR_ARG; }
     switch (option) {
     case EC_OPT_ALGO:
-        if (value < 0 || value > 2) { set_error("bad algo %lld", (long long)value); return EC_ERR_ARG; }
+        if (value < 0 || value > 3) { set_error("bad algo %lld", (long long)value); return EC_ERR_ARG; }
         ctx->algo = (int)value;
         return EC_OK;
     case EC_OPT_VALIDATE: ctx->validate = value ? 1 : 0; return EC_OK;
@@ -397,6 +508,8 @@ int64_t ec_selfcheck_rules(void)
     }
     for (auto &x : th) x.join();
     for (auto v : part) bad += v;
+    // planar per-voxel form (ec_slice.h) against the vertex tables
+    bad += selfcheck_planar(t3);
     // four-pixel byte-mask evaluation (fast 2D kernel) against the scalar closed form
     {
         uint64_t r2 = 0x2545F4914F6CDD1Dull;

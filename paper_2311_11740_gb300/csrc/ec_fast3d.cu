@@ -73,7 +73,9 @@ constexpr size_t stage_bytes(int mode)
                                                          : 0;
 }
 
-template <typename T, int MODE, bool PER, int DM, int SCHED = 0>
+// SLICE: count with the planar form of ec_slice.h (two planes in registers)
+// instead of the 26-neighbour form (three planes); same staging and schedule.
+template <typename T, int MODE, bool PER, int DM, int SCHED = 0, bool SLICE = false>
 __global__ void __launch_bounds__(kThreads, EC_FAST_MIN_BLOCKS)
 k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
 {
@@ -188,7 +190,26 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
         c.interior = c.x0 >= 4 && c.x0 + TXF + 4 <= p.W;
         __syncthreads();   // the previous item is done with both rings
         c.base = seq;
-        if constexpr (TMA) {
+        if constexpr (SLICE) {
+            if constexpr (TMA) {
+                if (threadIdx.x == 0) {
+                    for (int q = 0; q < NS - 2; q++) {
+                        const int pz = c.z0 - 1 + q;
+                        if (pz > c.z1) break;
+                        const uint32_t slot = (c.base + q) % NS;
+                        mbar_expect_tx(&c.bars[slot], BX * BY * 4);
+                        tma_load_plane(c.fring + slot * FSTRIDE, &tmap, c.x0 - 4, c.y0 - 1, pz, &c.bars[slot]);
+                        c.inflight |= 1u << slot;
+                    }
+                }
+                if (!walk_slice_tma<T, PER, DM>(c, &tmap)) return;
+            } else if constexpr (MODE == MODE_ASYNC || MODE == MODE_COVER) {
+                constexpr int STG = MODE == MODE_ASYNC ? STG_ALIGNED : STG_COVER;
+                if (!walk_slice_async2<T, PER, DM, STG>(c)) return;
+            } else {
+                if (!walk_slice_plain<T, PER, DM>(c)) return;
+            }
+        } else if constexpr (TMA) {
             // planes z0-1 .. z0+NS-4 now; the barrier steps request the rest
             if (threadIdx.x == 0) {
                 for (int q = 0; q < NS - 2; q++) {
@@ -238,9 +259,9 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
         for (int i = threadIdx.x; i < p.nd * L; i += kThreads) {
             // global rows are [nd][L]; level L of the interleaved layout is dropped
             int v;
-            if constexpr (interleaved_hist<DM, SCHED>()) {
+            if constexpr (SLICE || interleaved_hist<DM, SCHED>()) {
                 const int r = i / L, k = i - r * L;
-                v = c.sh_hist[k * dm_nd<DM>() + r];
+                v = c.sh_hist[k * (DM ? dm_nd<DM>() : p.nd) + r];
             } else {
                 v = c.sh_hist[i];
             }
@@ -253,6 +274,10 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
 
 }  // namespace fast3d
 
+namespace fast3d {
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
+}
+
 int launch_uniform_check(const float *thr, int32_t L, int *uni, cudaStream_t s)
 {
     fast3d::k_uniform_check<<<1, 256, 0, s>>>(thr, L, uni);
@@ -260,9 +285,14 @@ int launch_uniform_check(const float *thr, int32_t L, int *uni, cudaStream_t s)
     return EC_OK;
 }
 
+void *tma_encode_fn()
+{
+    return (void *)fast3d::encode_fn();
+}
+
 namespace fast3d {
 
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static bool tried = false;
@@ -292,11 +322,11 @@ static size_t smem_bytes(int mode, int dtype_size, int nd, int L, bool smem_hist
     return b;
 }
 
-template <typename T, int MODE, bool PER, int DM = 0, int SCHED = 0>
+template <typename T, int MODE, bool PER, int DM = 0, int SCHED = 0, bool SLICE = false>
 static int launch_t(const CUtensorMap &map, const Params &p, size_t smem, int num_sms, int items, int grid_override,
                     cudaStream_t s)
 {
-    auto kern = k_voxel3d_fast<T, MODE, PER, DM, SCHED>;
+    auto kern = k_voxel3d_fast<T, MODE, PER, DM, SCHED, SLICE>;
     EC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
@@ -308,12 +338,26 @@ static int launch_t(const CUtensorMap &map, const Params &p, size_t smem, int nu
     return EC_OK;
 }
 
+// Planar-form launches (shared-memory histogram): compile-time histogram rows
+// for the common descriptor sets, run-time rows otherwise.
+template <typename T, int MODE>
+static int launch_slice(const CUtensorMap &map, const Params &p, uint32_t desc, bool per, size_t smem, int num_sms,
+                        int items, int grid_override, cudaStream_t s)
+{
+    if (desc == 1u) return launch_t<T, MODE, false, 1, 0, true>(map, p, smem, num_sms, items, grid_override, s);
+    if (desc == 13u) return launch_t<T, MODE, false, 13, 0, true>(map, p, smem, num_sms, items, grid_override, s);
+    if (desc == 15u) return launch_t<T, MODE, true, 15, 0, true>(map, p, smem, num_sms, items, grid_override, s);
+    return per ? launch_t<T, MODE, true, 0, 0, true>(map, p, smem, num_sms, items, grid_override, s)
+               : launch_t<T, MODE, false, 0, 0, true>(map, p, smem, num_sms, items, grid_override, s);
+}
+
 // Plain-load and cp.async modes: compile-time histogram rows for the common
 // descriptor sets on the cp.async path, run-time rows otherwise.
 template <typename T, int MODE>
 static int launch_loads(const CUtensorMap &map, const Params &p, uint32_t desc, bool per, size_t smem, int num_sms,
                         int items, int grid_override, cudaStream_t s)
 {
+    if (p.smem_hist && p.planar) return launch_slice<T, MODE>(map, p, desc, per, smem, num_sms, items, grid_override, s);
     if constexpr (MODE == MODE_ASYNC || MODE == MODE_COVER) {
         if (p.smem_hist) {
             if (desc == 1u) return launch_t<T, MODE, false, 1>(map, p, smem, num_sms, items, grid_override, s);
@@ -333,6 +377,11 @@ int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, 
                    int grid_override, int num_sms, int *err_flag, cudaStream_t s, const int zrange[4])
 {
     using namespace fast3d;
+    if (ha.planar && ha.schedule <= 1) {
+        // float32 TMA fields with up to 1024 levels: two stacked quads per thread
+        const int rc = launch_planar_3d(field, dims, ba, ha, tile_z, grid_override, num_sms, err_flag, s, zrange);
+        if (rc != EC_ERR_UNSUPPORTED) return rc;
+    }
     if (ba.L > kMaxFastL3 || dims[0] > INT32_MAX / 2 || dims[1] > INT32_MAX / 2 || dims[2] > INT32_MAX / 2)
         return EC_ERR_UNSUPPORTED;
     Params p{};
@@ -389,6 +438,8 @@ int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, 
         }
     }
     if (ha.schedule == 3 && ha.smem_hist && tma && (desc == 13u || desc == 15u)) p.pairs = 1;
+    // the planar form needs the block histogram and the one-atomic schedule
+    p.planar = ha.planar && ha.smem_hist && !p.agg && !p.pairs ? 1 : 0;
     // without TMA, rows are staged with 16-byte cp.async chunks when the field
     // starts 16-byte aligned: whole rows if every row does too, else the
     // aligned cover of each row
@@ -399,6 +450,8 @@ int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, 
     switch (ba.dtype) {
     case EC_F32: {
         const size_t smem = smem_bytes<float>(mode, dsz, p.nd, p.L, p.smem_hist != 0, ba.thr != nullptr, p.pairs != 0);
+        if (tma && p.smem_hist && p.planar)
+            return launch_slice<float, MODE_TMA>(map, p, desc, per, smem, num_sms, items, grid_override, s);
         if (tma && p.smem_hist && !p.agg) {
             // descriptor sets with compile-time histogram rows
             if (p.pairs) {

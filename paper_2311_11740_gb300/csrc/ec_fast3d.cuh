@@ -8,6 +8,7 @@
 
 #include "ec_internal.h"
 #include "ec_rules.h"
+#include "ec_slice.h"
 #include "ec_swar.h"
 
 namespace ec {
@@ -59,6 +60,7 @@ struct Params {
     const int *uni;        // [0] = 1 if the uniform-spacing guess is exact, [1], [2] = its scale and offset (float bits)
     int agg;               // 1: warp-aggregated shared-memory updates (lanes grouped by level)
     int pairs;             // 1: two descriptors per 32-bit word, two lane-parity copies (see PairHist)
+    int planar;            // 1: count with the planar form (ec_slice.h); needs the shared histogram
 };
 
 // ------------------------------------------------------------- mbarriers
@@ -566,15 +568,16 @@ __device__ __forceinline__ void count_plane(Ctx<T> &c, uint32_t (&win)[3][3][5],
 // One step of the z walk with plain loads: bin plane s+2 into the key ring
 // (one barrier per plane), then count plane s.  R = t mod 3, s = z0 - 3 + t.
 // Returns false if the block must stop.
-template <typename T, bool PER, int R, int DM, int SCHED = 0>
-__device__ __forceinline__ bool zstep(Ctx<T> &c, uint32_t (&win)[3][3][5], int t)
+// Barrier step of the plain-load z walk at s = z0 - 3 + t: synchronise and
+// bin plane s+2 into the key ring (one barrier per plane).  Returns false if
+// the block must stop.
+template <typename T>
+__device__ __forceinline__ bool plain_barrier(Ctx<T> &c, int s)
 {
-    const int s = c.z0 - 3 + t;
     const int pb = s + 2;
     const int L = c.p.L;
     __syncthreads();
     if (*c.abort_flag) return false;
-    // ---- bin plane pb
     if (pb <= c.z1) {
         uint32_t *kp = c.kring + (uint32_t)((pb + 8) % NK) * KWORDS;
         if (pb < c.p.zv0 || pb >= c.p.zv1) {
@@ -595,6 +598,17 @@ __device__ __forceinline__ bool zstep(Ctx<T> &c, uint32_t (&win)[3][3][5], int t
             }
         }
     }
+    return true;
+}
+
+// One step of the z walk with plain loads: bin plane s+2 into the key ring
+// (plain_barrier), then count plane s.  R = t mod 3, s = z0 - 3 + t.
+// Returns false if the block must stop.
+template <typename T, bool PER, int R, int DM, int SCHED = 0>
+__device__ __forceinline__ bool zstep(Ctx<T> &c, uint32_t (&win)[3][3][5], int t)
+{
+    const int s = c.z0 - 3 + t;
+    if (!plain_barrier(c, s)) return false;
     count_plane<T, PER, R, DM, SCHED>(c, win, s);
     return true;
 }
@@ -621,59 +635,75 @@ __device__ __forceinline__ void drain_tma(Ctx<T> &c)
 // barrier earlier) and counts plane h.  Key ring: between two barriers the
 // block reads planes h+1, h+2 and writes h+3, h+4: four distinct slots.
 // Returns false if the block must stop.
-template <typename T, bool PER, int R, int DM, int SCHED = 0>
-__device__ __forceinline__ bool zstep_tma(Ctx<T> &c, const CUtensorMap *tmap, uint32_t (&win)[3][3][5], int t)
+// Barrier step of the TMA z walk (float32 fields) at h = z0 - 4 + t, t even:
+// thread 0 waits for the staged float planes h+3 and h+4, the block
+// synchronises, thread 0 requests planes h+NS+1 and h+NS+2 into the ring
+// slots of planes h+1 and h+2 (binned before this barrier), and the block bins
+// planes h+3 and h+4.  Returns false if the block must stop.
+template <typename T>
+__device__ __forceinline__ bool tma_barrier(Ctx<T> &c, const CUtensorMap *tmap, int h)
 {
-    const int h = c.z0 - 4 + t;
     const int L = c.p.L;
-    if ((t & 1) == 0) {
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int q = 3; q <= 4; q++) {
-                const int pb = h + q;
-                if (pb > c.z1) break;
-                const uint32_t slot = (c.base + (uint32_t)(pb - (c.z0 - 1))) % NS;
-                if (!mbar_wait(&c.bars[slot], (c.parity >> slot) & 1u)) {
-                    *c.abort_flag = 1;
-                    atomicOr(c.p.err, 4);
-                    break;
-                }
-                c.parity ^= 1u << slot;
-                c.inflight &= ~(1u << slot);
-            }
-        }
-        __syncthreads();
-        if (*c.abort_flag) {
-            if (threadIdx.x == 0) drain_tma(c);
-            return false;
-        }
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int q = NS + 1; q <= NS + 2; q++) {
-                const int pi = h + q;
-                if (pi > c.z1) break;
-                const uint32_t slot = (c.base + (uint32_t)(pi - (c.z0 - 1))) % NS;
-                mbar_expect_tx(&c.bars[slot], BX * BY * 4);
-                tma_load_plane(c.fring + slot * FSTRIDE, tmap, c.x0 - 4, c.y0 - 1, pi, &c.bars[slot]);
-                c.inflight |= 1u << slot;
-            }
-        }
-        // ---- bin planes h+3 (extra pairs on threads 0-99) and h+4 (threads 128-227)
+    if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 3; q <= 4; q++) {
             const int pb = h + q;
             if (pb > c.z1) break;
-            uint32_t *kp = c.kring + (uint32_t)((pb + 8) % NK) * KWORDS;
-            if (pb < c.p.zv0 || pb >= c.p.zv1) {
-                fill_never(kp, L);
-            } else {
-                const float *fp = c.fring + ((c.base + (uint32_t)(pb - (c.z0 - 1))) % NS) * FSTRIDE;
-                const bool extra = (q == 3) == (threadIdx.x < 128);
-                if (c.fb.uniform) bin_plane_f32<true>(kp, fp, c, extra);
-                else bin_plane_f32<false>(kp, fp, c, extra);
+            const uint32_t slot = (c.base + (uint32_t)(pb - (c.z0 - 1))) % NS;
+            if (!mbar_wait(&c.bars[slot], (c.parity >> slot) & 1u)) {
+                *c.abort_flag = 1;
+                atomicOr(c.p.err, 4);
+                break;
             }
+            c.parity ^= 1u << slot;
+            c.inflight &= ~(1u << slot);
         }
     }
+    __syncthreads();
+    if (*c.abort_flag) {
+        if (threadIdx.x == 0) drain_tma(c);
+        return false;
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = NS + 1; q <= NS + 2; q++) {
+            const int pi = h + q;
+            if (pi > c.z1) break;
+            const uint32_t slot = (c.base + (uint32_t)(pi - (c.z0 - 1))) % NS;
+            mbar_expect_tx(&c.bars[slot], BX * BY * 4);
+            tma_load_plane(c.fring + slot * FSTRIDE, tmap, c.x0 - 4, c.y0 - 1, pi, &c.bars[slot]);
+            c.inflight |= 1u << slot;
+        }
+    }
+    // ---- bin planes h+3 (extra pairs on threads 0-99) and h+4 (threads 128-227)
+#pragma unroll
+    for (int q = 3; q <= 4; q++) {
+        const int pb = h + q;
+        if (pb > c.z1) break;
+        uint32_t *kp = c.kring + (uint32_t)((pb + 8) % NK) * KWORDS;
+        if (pb < c.p.zv0 || pb >= c.p.zv1) {
+            fill_never(kp, L);
+        } else {
+            const float *fp = c.fring + ((c.base + (uint32_t)(pb - (c.z0 - 1))) % NS) * FSTRIDE;
+            const bool extra = (q == 3) == (threadIdx.x < 128);
+            if (c.fb.uniform) bin_plane_f32<true>(kp, fp, c, extra);
+            else bin_plane_f32<false>(kp, fp, c, extra);
+        }
+    }
+    return true;
+}
+
+// One half-step of the TMA z walk, counting plane h = z0 - 4 + t.  Every
+// other half-step (t even) is a barrier step (tma_barrier).  Every half-step
+// then loads key plane h+1 (binned at least one barrier earlier) and counts
+// plane h.  Key ring: between two barriers the block reads planes h+1, h+2
+// and writes h+3, h+4: four distinct slots.  Returns false if the block must
+// stop.
+template <typename T, bool PER, int R, int DM, int SCHED = 0>
+__device__ __forceinline__ bool zstep_tma(Ctx<T> &c, const CUtensorMap *tmap, uint32_t (&win)[3][3][5], int t)
+{
+    const int h = c.z0 - 4 + t;
+    if ((t & 1) == 0 && !tma_barrier(c, tmap, h)) return false;
     count_plane<T, PER, R, DM, SCHED>(c, win, h);
     return true;
 }
@@ -708,26 +738,51 @@ __device__ __forceinline__ bool zstep_async(Ctx<T> &c, uint32_t (&win)[3][3][5],
 // ago), synchronise, bin them, and start the copies of planes h+7 and h+8
 // (one group) into the slots of planes h+1 and h+2, binned one barrier step
 // ago.  Returns false if the block must stop.
+// Barrier step of the two-plane cp.async walk at h = z0 - 4 + t, t even:
+// wait for this thread's copies of planes h+3 and h+4 (issued two barrier
+// steps ago), synchronise, bin them, and start the copies of planes h+7 and
+// h+8 (one group) into the slots of planes h+1 and h+2, binned one barrier
+// step ago.  Returns false if the block must stop.
+template <typename T, int STG>
+__device__ __forceinline__ bool async2_barrier(Ctx<T> &c, int h)
+{
+    cp_async_wait<1>();
+    __syncthreads();
+    if (*c.abort_flag) return false;
+#pragma unroll
+    for (int q = 3; q <= 4; q++) {
+        const int pb = h + q;
+        if (pb > c.z1) break;
+        uint32_t *kp = c.kring + (uint32_t)((pb + 8) % NK) * KWORDS;
+        if (pb < c.p.zv0 || pb >= c.p.zv1) fill_never(kp, c.p.L);
+        else bin_plane_raw2<T, STG>(c, pb, kp, (q == 3) == (threadIdx.x < 128));
+    }
+    copy_plane<T, STG, NRAWP2, false>(c, h + 7, h + 7 <= c.z1);
+    copy_plane<T, STG, NRAWP2, false>(c, h + 8, h + 8 <= c.z1);
+    cp_async_commit();
+    return true;
+}
+
+// Start the copies of planes z0-1 .. z0+2 (two groups) for the two-plane walk.
+template <typename T, int STG>
+__device__ __forceinline__ void async2_prologue(Ctx<T> &c)
+{
+    copy_plane<T, STG, NRAWP2, false>(c, c.z0 - 1, true);
+    copy_plane<T, STG, NRAWP2, false>(c, c.z0, c.z0 <= c.z1);
+    cp_async_commit();
+    copy_plane<T, STG, NRAWP2, false>(c, c.z0 + 1, c.z0 + 1 <= c.z1);
+    copy_plane<T, STG, NRAWP2, false>(c, c.z0 + 2, c.z0 + 2 <= c.z1);
+    cp_async_commit();
+}
+
+// One half-step of the two-plane cp.async walk (same plane schedule as
+// zstep_tma), counting plane h = z0 - 4 + t; barrier steps (t even) run
+// async2_barrier first.  Returns false if the block must stop.
 template <typename T, bool PER, int R, int DM, int SCHED, int STG>
 __device__ __forceinline__ bool zstep_async2(Ctx<T> &c, uint32_t (&win)[3][3][5], int t)
 {
     const int h = c.z0 - 4 + t;
-    if ((t & 1) == 0) {
-        cp_async_wait<1>();
-        __syncthreads();
-        if (*c.abort_flag) return false;
-#pragma unroll
-        for (int q = 3; q <= 4; q++) {
-            const int pb = h + q;
-            if (pb > c.z1) break;
-            uint32_t *kp = c.kring + (uint32_t)((pb + 8) % NK) * KWORDS;
-            if (pb < c.p.zv0 || pb >= c.p.zv1) fill_never(kp, c.p.L);
-            else bin_plane_raw2<T, STG>(c, pb, kp, (q == 3) == (threadIdx.x < 128));
-        }
-        copy_plane<T, STG, NRAWP2, false>(c, h + 7, h + 7 <= c.z1);
-        copy_plane<T, STG, NRAWP2, false>(c, h + 8, h + 8 <= c.z1);
-        cp_async_commit();
-    }
+    if ((t & 1) == 0 && !async2_barrier<T, STG>(c, h)) return false;
     count_plane<T, PER, R, DM, SCHED>(c, win, h);
     return true;
 }
@@ -736,12 +791,7 @@ __device__ __forceinline__ bool zstep_async2(Ctx<T> &c, uint32_t (&win)[3][3][5]
 template <typename T, bool PER, int DM, int SCHED, int STG>
 __device__ __forceinline__ bool walk_item_async2(Ctx<T> &c, uint32_t (&win)[3][3][5])
 {
-    copy_plane<T, STG, NRAWP2, false>(c, c.z0 - 1, true);
-    copy_plane<T, STG, NRAWP2, false>(c, c.z0, c.z0 <= c.z1);
-    cp_async_commit();
-    copy_plane<T, STG, NRAWP2, false>(c, c.z0 + 1, c.z0 + 1 <= c.z1);
-    copy_plane<T, STG, NRAWP2, false>(c, c.z0 + 2, c.z0 + 2 <= c.z1);
-    cp_async_commit();
+    async2_prologue<T, STG>(c);
     const int nsteps = c.z1 - c.z0 + 4;
     bool ok = true;
     for (int t = 0; ok && t < nsteps; t += 3) {
@@ -751,6 +801,136 @@ __device__ __forceinline__ bool walk_item_async2(Ctx<T> &c, uint32_t (&win)[3][3
     }
     cp_async_wait<0>();
     return ok;
+}
+
+// ------------------------------------------- planar (slice) counting, ec_slice.h
+
+// Load the rows y-1, y, y+1 of key plane `plane` around this thread's quad.
+template <typename T>
+__device__ __forceinline__ void load_rows5(const Ctx<T> &c, int plane, Row5 (&W)[3])
+{
+    const uint32_t *kp = c.kring + (uint32_t)((plane + 8) % NK) * KWORDS;
+#pragma unroll
+    for (int dy = 0; dy < 3; dy++) {
+        const uint32_t *r = kp + (c.tr + dy) * KP + 2 * c.tc;
+        const uint2 a = *(const uint2 *)r, b = *(const uint2 *)(r + 2);
+        W[dy].a = __byte_perm(a.x, a.y, 0x5432);   // keys x-1, x
+        W[dy].b = a.y;                             // x, x+1
+        W[dy].c = __byte_perm(a.y, b.x, 0x5432);   // x+1, x+2
+        W[dy].d = b.x;                             // x+2, x+3
+        W[dy].e = __byte_perm(b.x, b.y, 0x5432);   // x+3, x+4
+    }
+}
+
+// Add the changes of the quad's four voxels at their levels (key pairs kb =
+// voxels 0, 1 and kd = voxels 2, 3).  Histogram rows interleaved per level,
+// [L+1][nd], with the never-active level L in its own (discarded) slot.
+// DM != 0: descriptor rows fixed at compile time; DM == 0: rows[] at run time.
+template <int DM>
+__device__ __forceinline__ void slice_hist(int *h, int nd, const int (&rows)[kMaxDesc], uint32_t kb, uint32_t kd,
+                                           const SliceOut &o)
+{
+    const uint32_t key[4] = {kb & 0xFFFFu, kb >> 16, kd & 0xFFFFu, kd >> 16};
+    const int ecv[4] = {sbyte<0>(o.ec), sbyte<1>(o.ec), sbyte<2>(o.ec), sbyte<3>(o.ec)};
+    if constexpr (DM != 0) {
+        constexpr int ND = dm_nd<DM>();
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+            int *const e = h + key[v] * ND;
+            if (DM & 1) atomicAdd(e + dm_row<DM, 0>(), ecv[v]);
+            if (DM & 2) {
+                const int pv[4] = {sbyte<0>(o.per), sbyte<1>(o.per), sbyte<2>(o.per), sbyte<3>(o.per)};
+                atomicAdd(e + dm_row<DM, 1>(), pv[v]);
+            }
+            if (DM & 4) {
+                const int av[4] = {sbyte<0>(o.area), sbyte<1>(o.area), sbyte<2>(o.area), sbyte<3>(o.area)};
+                atomicAdd(e + dm_row<DM, 2>(), av[v]);
+            }
+            if (DM & 8) atomicAdd(e + dm_row<DM, 3>(), 1);
+        }
+    } else {
+        const int pv[4] = {sbyte<0>(o.per), sbyte<1>(o.per), sbyte<2>(o.per), sbyte<3>(o.per)};
+        const int av[4] = {sbyte<0>(o.area), sbyte<1>(o.area), sbyte<2>(o.area), sbyte<3>(o.area)};
+#pragma unroll
+        for (int v = 0; v < 4; v++) {
+            int *const e = h + key[v] * nd;
+            if (rows[0] >= 0) atomicAdd(e + rows[0], ecv[v]);
+            if (rows[1] >= 0) atomicAdd(e + rows[1], pv[v]);
+            if (rows[2] >= 0) atomicAdd(e + rows[2], av[v]);
+            if (rows[3] >= 0) atomicAdd(e + rows[3], 1);
+        }
+    }
+}
+
+// One step of a planar walk at plane h (same plane schedule as the
+// 26-neighbour walks): load key plane h+1 into Q; at h = z0 - 1 start the
+// state from planes z0 - 1 (P) and z0 (Q); from h = z0 on, count plane h.
+template <typename T, bool PER, int DM>
+__device__ __forceinline__ void slice_step(Ctx<T> &c, Row5 (&P)[3], Row5 (&Q)[3], SliceState &st, int h)
+{
+    if (h >= c.z0 - 2) load_rows5(c, h + 1, Q);
+    if (h == c.z0 - 1) {
+        slice_begin<PER>(P, Q, st);
+    } else if (h >= c.z0) {
+        constexpr bool AREA = DM == 0 || (DM & 4) != 0;
+        const SliceOut o = slice_quad<AREA, PER>(P, Q, st);
+        slice_hist<DM>(c.sh_hist, c.p.nd, c.p.rows, P[1].b, P[1].d, o);
+    }
+}
+
+// Planar walks of one item (planes z0-1 .. z1 binned, z0 .. z1-1 counted).
+// The two window registers alternate between plane h and h+1, so the loop
+// runs two half-steps per turn; barrier steps are the even ones.
+template <typename T, bool PER, int DM>
+__device__ __forceinline__ bool walk_slice_tma(Ctx<T> &c, const CUtensorMap *tmap)
+{
+    Row5 W0[3], W1[3];
+    SliceState st{};
+    const int nsteps = c.z1 - c.z0 + 4;
+    for (int t = 0; t < nsteps; t += 2) {
+        const int h = c.z0 - 4 + t;
+        if (!tma_barrier(c, tmap, h)) return false;
+        slice_step<T, PER, DM>(c, W0, W1, st, h);
+        if (t + 1 < nsteps) slice_step<T, PER, DM>(c, W1, W0, st, h + 1);
+    }
+    return true;
+}
+
+template <typename T, bool PER, int DM, int STG>
+__device__ __forceinline__ bool walk_slice_async2(Ctx<T> &c)
+{
+    Row5 W0[3], W1[3];
+    SliceState st{};
+    async2_prologue<T, STG>(c);
+    const int nsteps = c.z1 - c.z0 + 4;
+    bool ok = true;
+    for (int t = 0; ok && t < nsteps; t += 2) {
+        const int h = c.z0 - 4 + t;
+        ok = async2_barrier<T, STG>(c, h);
+        if (!ok) break;
+        slice_step<T, PER, DM>(c, W0, W1, st, h);
+        if (t + 1 < nsteps) slice_step<T, PER, DM>(c, W1, W0, st, h + 1);
+    }
+    cp_async_wait<0>();
+    return ok;
+}
+
+template <typename T, bool PER, int DM>
+__device__ __forceinline__ bool walk_slice_plain(Ctx<T> &c)
+{
+    Row5 W0[3], W1[3];
+    SliceState st{};
+    const int nsteps = c.z1 - c.z0 + 3;
+    for (int t = 0; t < nsteps; t += 2) {
+        const int s = c.z0 - 3 + t;
+        if (!plain_barrier(c, s)) return false;
+        slice_step<T, PER, DM>(c, W0, W1, st, s);
+        if (t + 1 < nsteps) {
+            if (!plain_barrier(c, s + 1)) return false;
+            slice_step<T, PER, DM>(c, W1, W0, st, s + 1);
+        }
+    }
+    return true;
 }
 
 }  // namespace fast3d

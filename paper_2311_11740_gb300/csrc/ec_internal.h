@@ -53,6 +53,7 @@ struct HistArgs {
     long long *hist;    // global int64 [nd][L]
     int smem_hist;      // 1: block-private shared-memory int32 histogram, flushed at the end
     int schedule = 0;   // shared-memory update schedule: 0 auto, 1 one atomic per voxel, 2 warp-aggregated
+    int planar = 0;     // 3D per-voxel kernels: count with the planar form (ec_slice.h) where it applies
 };
 
 // Launch helpers implemented in ec_kernels.cu.  All are stream-ordered and
@@ -68,6 +69,13 @@ int launch_curve_2d(const void *field, const int64_t dims[2], const BinArgs &ba,
 // as never active (slab halos at the field's ends).
 int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha, int tile_z,
                    int grid_override, int num_sms, int *err_flag, cudaStream_t s, const int zrange[4] = nullptr);
+// The planar-form kernel for float32 fields staged by TMA (at most 1024
+// levels; descriptor sets EC, EC|AREA|VOLUME, all four); EC_ERR_UNSUPPORTED
+// without launching for anything else.
+int launch_planar_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha, int tile_z,
+                     int grid_override, int num_sms, int *err_flag, cudaStream_t s, const int zrange[4] = nullptr);
+// cuTensorMapEncodeTiled from the driver (nullptr if unavailable).
+void *tma_encode_fn();
 // The fast per-pixel 2D kernel; EC_ERR_UNSUPPORTED without launching when a
 // request does not fit it (more than 32767 levels).
 int launch_fast_2d(const void *field, const int64_t dims[2], const BinArgs &ba, const HistArgs &ha, int connectivity,
@@ -87,7 +95,7 @@ void row_scales(int ndim, int algo, uint32_t desc, int32_t out[kMaxDesc]);
 constexpr size_t kSmemHistBudget = 96 * 1024;
 inline bool use_smem_hist(int nd, int32_t L) { return (size_t)nd * ((size_t)L + 1) * 4 <= kSmemHistBudget; }
 
-enum { ALGO_AUTO = 0, ALGO_VOXEL = 1, ALGO_VERTEX = 2 };
+enum { ALGO_AUTO = 0, ALGO_VOXEL = 1, ALGO_VERTEX = 2, ALGO_PLANAR = 3 };
 
 // Argument checks shared by every curve entry point.
 int validate_request(int ndim, const void *field, const int64_t *dims, int dtype, const void *thr, int32_t L,

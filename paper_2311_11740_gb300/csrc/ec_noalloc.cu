@@ -17,7 +17,14 @@
 //     Calls whose work overlaps on the GPU (two streams, or two host threads)
 //     race on it and give wrong curves: serialise them.
 //   * The first call on a device looks up the array's device address (with
-//     that device current); make that first call before any stream capture.
+//     that device current).  With CUDA's lazy module loading that lookup is
+//     what loads the library's device code on that device and reserves the
+//     array, so the first call may allocate and synchronise implicitly: make
+//     one warm-up call per device outside the latency-critical loop and
+//     before any stream capture.  Later calls allocate nothing.
+//   * Failures on the device (a bounded device wait that gave up) are not
+//     turned into a status code: the call does not synchronise, and the
+//     affected curve rows read INT64_MIN in every entry.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -85,16 +92,16 @@ extern "C" int ec_curve_3d_noalloc(const void *field_dev, const int64_t dims[3],
     int sms = 0;
     rc = setup_device(dev, &scratch, &sms);
     if (rc) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
-    int *flags = (int *)scratch;
-    long long *hist = (long long *)((char *)scratch + kNoallocFlagBytes);
-    EC_CUDA(cudaMemsetAsync(scratch, 0, kNoallocFlagBytes + entries * sizeof(long long), s));
-    const BinArgs ba{L, dtype, thresholds_dev};
-    const HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0};
-    rc = launch_fast_3d(field_dev, dims, ba, ha, 0, 0, sms, flags, s);
-    if (rc == EC_ERR_UNSUPPORTED) rc = launch_curve_3d(field_dev, dims, ba, ha, ALGO_VOXEL, 0, 0, sms, s);
-    if (rc) return rc;
-    int32_t scale[kMaxDesc];
-    row_scales(3, ALGO_VOXEL, descriptors, scale);
-    return launch_scan(hist, rows.nd, L, scale, out_dev, flags, s);
+    // the launch sequence of ec_curve_3d (reset, histogram kernels, scan) on
+    // the fixed array, which has the layout curve_scratch_bytes describes
+    static_assert(kNoallocBytes >= kNoallocFlagBytes + kNoallocHistEntries * sizeof(long long), "scratch layout");
+    if (curve_scratch_bytes(descriptors, L) > kNoallocBytes) {
+        set_error("scratch layout mismatch");
+        return EC_ERR_ARG;
+    }
+    CurvePlan plan;
+    plan.algo = ALGO_AUTO;
+    plan.num_sms = sms;
+    return enqueue_curve(plan, 3, field_dev, dims, dtype, thresholds_dev, L, connectivity, descriptors, out_dev,
+                         scratch, (cudaStream_t)stream);
 }

@@ -149,7 +149,8 @@ extern "C" int ec_curve_3d_stream(ec_ctx *ctx, const void *host_field, ec_slab_f
         if (rc) return rc;
         ba.uni_ready = 1;
     }
-    const HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0, ctx->hist_schedule};
+    HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0, ctx->hist_schedule};
+    ha.planar = ctx->algo == ALGO_AUTO || ctx->algo == ALGO_PLANAR;
     const int64_t nslabs = (d + S - 1) / S;
     for (int64_t i = 0; i < nslabs; i++) {
         const int b = (int)(i % nbuf);

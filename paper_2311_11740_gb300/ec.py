@@ -19,7 +19,7 @@ EC_U8, EC_U16, EC_F32 = 0, 1, 2
 EC_DESC_EC, EC_DESC_PERIMETER, EC_DESC_AREA, EC_DESC_VOLUME = 1, 2, 4, 8
 EC_OPT_ALGO, EC_OPT_VALIDATE, EC_OPT_TILE_Z, EC_OPT_GRID, EC_OPT_PROFILE, EC_OPT_HIST_SCHEDULE = 1, 2, 3, 4, 5, 6
 EC_OPT_AUTOTUNE = 7
-ALGO_AUTO, ALGO_VOXEL, ALGO_VERTEX = 0, 1, 2
+ALGO_AUTO, ALGO_VOXEL, ALGO_VERTEX, ALGO_PLANAR = 0, 1, 2, 3
 STATUS = {0: "EC_OK", 1: "EC_ERR_ARG", 2: "EC_ERR_DTYPE", 3: "EC_ERR_UNSUPPORTED", 4: "EC_ERR_OOM",
           5: "EC_ERR_CUDA", 6: "EC_ERR_TIMEOUT", 7: "EC_ERR_OVERFLOW", 8: "EC_ERR_BUSY"}
 

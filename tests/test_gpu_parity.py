@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 ALL2 = ec.EC_DESC_EC | ec.EC_DESC_PERIMETER | ec.EC_DESC_AREA
 ALL3 = ALL2 | ec.EC_DESC_VOLUME
-ALGOS = [ec.ALGO_VOXEL, ec.ALGO_VERTEX]
+ALGOS = [ec.ALGO_PLANAR, ec.ALGO_VOXEL, ec.ALGO_VERTEX]
 
 
 @pytest.fixture(scope="module")
@@ -85,6 +85,45 @@ def test_random_3d(ctx, shape, dtype):
     check(ctx, f, thr, L)
 
 
+# float32 fields whose rows are multiples of 4 floats and whose storage
+# starts 16-byte aligned take the TMA staging; with at most 1024 levels and
+# the descriptor sets EC, EC|AREA|VOLUME or all four they run on the kernel
+# with two stacked quads per thread (64 x 32 tiles).  Partial tiles in x, y
+# and z, odd heights (a thread's second row outside the field), one-plane
+# fields, uniform thresholds (spacing guess) and irregular ones.
+SHAPES3_TMA = [(1, 1, 4), (3, 1, 8), (2, 33, 68), (17, 31, 132), (70, 65, 64), (9, 64, 4), (5, 2, 196),
+               (130, 3, 12), (1, 32, 64), (33, 97, 100)]
+
+
+@pytest.mark.parametrize("shape", SHAPES3_TMA)
+@pytest.mark.parametrize("uniform", [True, False])
+def test_planar_tma_shapes(ctx, shape, uniform):
+    rng = np.random.default_rng(zlib.crc32(repr((shape, uniform, "tma")).encode()))
+    if uniform:
+        f = workloads.grf_nd(int(rng.integers(1 << 30)), shape, 1.5).numpy().astype(np.float32)
+        L = int(rng.integers(2, 1025))
+        thr = workloads.uniform_thresholds(float(f.min()), float(f.max()), L).numpy()
+    else:
+        f = rng.normal(size=shape).astype(np.float32)
+        L = int(rng.integers(1, 1025))
+        thr = np.sort(rng.normal(size=L)).astype(np.float32)
+    for desc in (1, 13, 15):
+        check(ctx, f, thr, L, desc=desc, algos=[ec.ALGO_PLANAR])
+
+
+def test_planar_tma_item_depths_and_constant_field(ctx):
+    """Work items of 1..7 and 64 planes; a constant field puts every voxel of a
+    block on one level, the largest count the packed area/volume words take
+    between two exchanges."""
+    f, thr = workloads.config3(n=68, nblobs=25, L=700)
+    f, thr = f.numpy(), thr.numpy()
+    for tz in (1, 2, 3, 5, 7, 64):
+        check(ctx, f, thr, 700, desc=13, algos=[ec.ALGO_PLANAR], tile_z=tz)
+    c = np.zeros((96, 64, 128), np.float32)
+    for desc in (13, 15):
+        check(ctx, c, np.array([-1.0, 0.0, 1.0], np.float32), 3, desc=desc, algos=[ec.ALGO_PLANAR])
+
+
 # Rows of 16-byte multiples take the cp.async staging (uint8 / uint16, and
 # float32 fields whose storage is not 16-byte aligned take plain loads);
 # partial tiles in x, y and z.
@@ -102,7 +141,7 @@ def test_random_3d_aligned_rows(ctx, shape, dtype):
         f = np.clip(smooth * 300 + 1000, 0, 2000).astype(np.uint16)
         L, thr = 700, np.sort(rng.integers(0, 2001, size=700)).astype(np.uint16)
     for desc in (1, 13, 15, 6):
-        check(ctx, f, thr, L, desc=desc, algos=[ec.ALGO_VOXEL])
+        check(ctx, f, thr, L, desc=desc, algos=[ec.ALGO_PLANAR, ec.ALGO_VOXEL])
 
 
 def test_3d_unaligned_float_pointer(ctx):
@@ -163,7 +202,7 @@ def test_wide_2d_strips(ctx, shape, dtype):
         L = 257
         thr = np.linspace(f.min(), f.max(), L).astype(np.float32)
     for conn in (8, 4):
-        check(ctx, f, thr, L, conn=conn, algos=[ec.ALGO_VOXEL])
+        check(ctx, f, thr, L, conn=conn, algos=[ec.ALGO_PLANAR, ec.ALGO_VOXEL])
 
 
 def test_2d_unaligned_field_pointer(ctx):
@@ -283,6 +322,15 @@ def test_config3_full_size(ctx):
     got = ec.curve(f, thr, descriptors=ALL3, ctx=ctx)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(got.cpu().numpy(), want)
+    # the benchmarked descriptor set (EC, area, volume: its own compiled
+    # instantiation), by both per-voxel forms; its rows are rows 0, 2, 3 of
+    # the all-descriptor curves
+    for algo in (ec.ALGO_AUTO, ec.ALGO_VOXEL):
+        ctx.set_option(ec.EC_OPT_ALGO, algo)
+        got13 = ec.curve(f, thr, descriptors=13, ctx=ctx)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(got13.cpu().numpy(), want[[0, 2, 3]], err_msg=f"algo {algo}")
+    ctx.set_option(ec.EC_OPT_ALGO, ec.ALGO_AUTO)
     # invariants that hold at any size
     assert want[0, -1] == 1 and want[3, -1] == 512 ** 3
 
@@ -313,7 +361,7 @@ def test_uniform_threshold_binning_edges(ctx, lo, hi, L):
     vals = np.concatenate([picks, np.nextafter(picks, np.float32(np.inf)),
                            np.nextafter(picks, np.float32(-np.inf)), special]).astype(np.float32)
     f = rng.permutation(np.resize(vals, 24 * 25 * 28)).astype(np.float32).reshape(24, 25, 28)
-    check(ctx, f, thr, L, algos=[ec.ALGO_VOXEL])
+    check(ctx, f, thr, L, algos=[ec.ALGO_PLANAR, ec.ALGO_VOXEL])
 
 
 @pytest.mark.parametrize("desc", [1, 5, 13, 15, 8, 2])

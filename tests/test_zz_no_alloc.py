@@ -41,6 +41,32 @@ def test_noalloc_matches_ec_curve_3d_on_two_calls(libec):
         np.testing.assert_array_equal(out_g.cpu().numpy(), want_g)
 
 
+def test_noalloc_equals_oracle_and_covers_every_kernel_branch(libec):
+    """Against the CPU oracle directly, on the fast kernel, on the generic
+    kernel the fast one hands over to (more levels than the fast kernel's
+    16-bit keys hold), and at exactly the scratch's 65536 histogram entries
+    (4 descriptors x 16384 levels: the global-histogram variant)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    rng = np.random.default_rng(12)
+    cases = []
+    f, thr = workloads.config3(n=40, nblobs=10, L=65)
+    cases.append((f.numpy(), thr.numpy(), 65, 15))
+    cases.append((rng.integers(0, 40000, size=(5, 9, 21)).astype(np.uint16), None, 32768, 9))
+    cases.append((rng.integers(0, 17000, size=(6, 11, 19)).astype(np.uint16), None, 16384, 15))
+    for fh, th, L, desc in cases:
+        want = oracle.ec_curves(fh, th, L, 26, desc)
+        fd = torch.from_numpy(fh.astype(np.int32)).cuda().to(torch.uint16) if fh.dtype == np.uint16 \
+            else torch.from_numpy(fh).cuda()
+        td = None if th is None else torch.from_numpy(th).cuda()
+        for _ in range(2):
+            out = torch.full(want.shape, -1, dtype=torch.int64, device="cuda")
+            assert _noalloc(fd, td, L, desc, out) == 0, ec.lib().ec_last_error()
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(out.cpu().numpy(), want, err_msg=f"L={L} desc={desc}")
+
+
 def test_noalloc_rejects_requests_beyond_its_scratch(libec):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
