@@ -144,6 +144,20 @@ def traffic_per_launch(summary=PROFILE_SUMMARY, sources=KERNEL_SOURCES):
 
 
 def cpu_baseline(field_cpu, thr_cpu, budget_s: float):
+    """The oracle on all host cores and on one core, each for about half of
+    `budget_s` (see cpu_baseline_once)."""
+    import oracle
+    full = cpu_baseline_once(field_cpu, thr_cpu, budget_s * 0.55)
+    oracle.set_threads(1)
+    try:
+        one = cpu_baseline_once(field_cpu, thr_cpu, budget_s * 0.45)
+    finally:
+        oracle.set_threads(0)
+    full["one_core"] = one
+    return full
+
+
+def cpu_baseline_once(field_cpu, thr_cpu, budget_s: float):
     """Time the oracle (as it stands) on a bounded sample of the workload:
     whole passes over the field (or over its first z-planes when one pass
     would exceed the budget), repeated until about `budget_s` seconds."""
@@ -302,6 +316,95 @@ def type_map_section(ec, ctx, field, thr, steps, with_cpu, budget_s):
                                          f"z-planes ({sample.size} voxels), scaled to 1024 levels "
                                          f"({t_bin:.2f} s + 1024 x {t_level:.3f} s)"}
     return out
+
+
+def configs_2d_section(ec, ctx, steps=20, with_cpu=True):
+    """The 2D workloads: a 256^2 uint8 field (256 identity levels; small,
+    so launch-latency bound: microseconds per request) and the 16384^2
+    field as uint8 (256 levels) and as float32 (1024 uniform thresholds),
+    EC + perimeter + area, 8-connectivity.  Per request: device time of the
+    whole request (memset, spacing check, histogram kernel, scan) and of the
+    histogram kernel alone, with its HBM roofline (1 or 4 bytes per pixel).
+    The oracle is timed on all host cores and on one core on a bounded
+    sample (the first rows of the field)."""
+    import numpy as np
+    import oracle
+    from paper_2311_11740_gb300 import workloads
+    peak, peak_kind = measured_peaks()
+    desc = ec.EC_DESC_EC | ec.EC_DESC_PERIMETER | ec.EC_DESC_AREA
+    out = {}
+    try:
+        g1 = workloads.config1(device="cuda")
+        o1 = torch_empty((3, 256))
+        ec.curve(g1, None, L=256, descriptors=desc, out=o1, ctx=ctx)
+        ctx.profile_read()
+        ms = time_device(lambda: ec.curve(g1, None, L=256, descriptors=desc, out=o1, ctx=ctx), 200)
+        kms, kl = ctx.profile_read()
+        kus = kms / max(kl, 1) * 1e3
+        want1 = oracle.ec_curves(g1.cpu().numpy(), None, 256, 8, desc)
+        c1 = {"workload": "256^2 uint8 smoothed GRF (seed 1, sigma 4), 256 identity levels, EC+perimeter+area",
+              "us_per_field": ms * 1e3, "kernel_avg_us": kus,
+              "roofline": {"bound": "hbm", "kernel": "k_pixel2d_fast", "achieved": 65536 / (kus * 1e-6) / 1e9,
+                           "peak": peak, "unit": "GB/s", "frac": 65536 / (kus * 1e-6) / 1e9 / peak,
+                           "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": 65536,
+                           "note": "64 KiB per request: launch-latency bound, not bandwidth bound"},
+              "identical": bool(np.array_equal(o1.cpu().numpy(), want1))}
+        if with_cpu:
+            c1["cpu_baseline"] = {}
+            for cores in (0, 1):
+                oracle.set_threads(cores)
+                h1 = g1.cpu().numpy()
+                t0, reps = time.perf_counter(), 0
+                while time.perf_counter() - t0 < 1.0:
+                    oracle.ec_curves(h1, None, 256, 8, desc)
+                    reps += 1
+                c1["cpu_baseline"]["all_cores" if cores == 0 else "one_core"] = {
+                    "us_per_field": (time.perf_counter() - t0) / reps * 1e6,
+                    "cores": oracle.num_threads(), "kind": "oracle", "sample": f"{reps} whole fields"}
+            oracle.set_threads(0)
+        out["config1"] = c1
+        u8, f32, thr = workloads.config2(device="cuda")
+        c2 = {"workload": "16384^2 smoothed GRF (seed 2, sigma 16, periodic FFT): uint8 with 256 identity levels "
+                          "and the float32 copy with 1024 uniform thresholds; EC+perimeter+area"}
+        for name, fld, t, Lr, nbytes in (("u8", u8, None, 256, u8.numel()), ("f32", f32, thr, 1024, f32.numel() * 4)):
+            o = torch_empty((3, Lr))
+            ec.curve(fld, t, L=Lr, descriptors=desc, out=o, ctx=ctx)
+            ctx.profile_read()
+            ms = time_device(lambda: ec.curve(fld, t, L=Lr, descriptors=desc, out=o, ctx=ctx), steps)
+            kms, kl = ctx.profile_read()
+            kus = kms / max(kl, 1) * 1e3
+            ach = nbytes / (kus * 1e-6) / 1e9
+            c2[name] = {"ms_per_step": ms, "value": fld.numel() / ms / 1e6, "unit": "Gpixels/s",
+                        "roofline": {"bound": "hbm", "kernel": "k_pixel2d_fast", "achieved": ach, "peak": peak,
+                                     "unit": "GB/s", "frac": ach / peak, "peak_source": peak_kind, "traffic": None,
+                                     "kernel_avg_us": kus, "algorithmic_bytes_per_launch": nbytes}}
+            # invariants at full size: the top level holds every pixel
+            top = o[:, -1].cpu().numpy()
+            c2[name]["top_level_invariants"] = bool(top[0] == 1 and top[1] == 2 * (16384 + 16384)
+                                                    and top[2] == 16384 * 16384)
+        if with_cpu:
+            rows = 1024
+            sample = np.ascontiguousarray(u8[:rows].cpu().numpy())
+            c2["cpu_baseline"] = {}
+            for cores in (0, 1):
+                oracle.set_threads(cores)
+                t0 = time.perf_counter()
+                oracle.ec_curves(sample, None, 256, 8, desc)
+                dt = time.perf_counter() - t0
+                c2["cpu_baseline"]["all_cores" if cores == 0 else "one_core"] = {
+                    "value": sample.size / dt / 1e9, "unit": "Gpixels/s", "cores": oracle.num_threads(),
+                    "kind": "oracle", "sample": f"the first {rows} rows of the uint8 field ({sample.size} pixels)"}
+            oracle.set_threads(0)
+        out["config2"] = c2
+        del u8, f32, thr
+    except Exception as e:   # the optional leg must not cost the line
+        out["error"] = f"{type(e).__name__}: {e}"
+    return out
+
+
+def torch_empty(shape):
+    import torch
+    return torch.empty(shape, dtype=torch.int64, device="cuda")
 
 
 def file_stream_section(ec, ctx, field, thr, want, reps=3):
@@ -548,6 +651,8 @@ def main():
     all_ms = time_device(lambda: ec.curve(field, thr, descriptors=DESC_ALL, out=out_all, ctx=ctx), 50)
     ctx.profile_read()
     file_stream = None if rank != 0 else file_stream_section(ec, ctx, field, thr, out.cpu().numpy())
+    configs_2d = None if (args.no_batch or rank != 0) else configs_2d_section(ec, ctx,
+                                                                               with_cpu=not args.no_cpu_baseline)
     type_map = None if (args.no_type_map or rank != 0) else type_map_section(
         ec, ctx, field, thr, 20, not args.no_cpu_baseline, args.cpu_budget)
     batched = None if (args.no_batch or rank != 0) else batched_vs_per_field(ec, ctx, args.batch_requests)
@@ -577,6 +682,8 @@ def main():
         "all_descriptors": {"descriptors": "EC+perimeter+area+volume", "ms_per_step": all_ms,
                             "value": vox / all_ms / 1e6, "unit": "Gvoxels/s"},
         "file_stream": file_stream,
+        "config1": None if configs_2d is None else configs_2d.get("config1"),
+        "config2": None if configs_2d is None else configs_2d.get("config2"),
         "type_map": type_map,
         "batched_vs_per_field": batched,
         "realtime_frames": frames,

@@ -33,7 +33,12 @@
  *    length (Table 2's "Perimeter" column summed over vertices); volume counts
  *    active voxels.  Cells outside the field are never active.
  *  - connectivity: 2D 8 (the paper's choice, Sec. 2) or 4 (Table 1's 4-C
- *    columns); 3D 26 (the paper's choice).  3D 6 -> EC_ERR_UNSUPPORTED.
+ *    columns); 3D 26 (the paper's choice) or 6.  Only the EC curve depends
+ *    on it.  Under 6-connectivity a cell of the grid is in the complex when
+ *    ALL its incident voxels are active, so the EC is #voxels - #face-adjacent
+ *    pairs + #2x2 squares - #2x2x2 cubes of the active set (the paper gives a
+ *    second connectivity only in 2D; in 2D the same reading is Table 1's 4-C
+ *    column).  6-connected requests run on the generic kernels.
  *  - Device pointers (suffix _dev) must be device-accessible on the context's
  *    device.  The caller owns every buffer; the library never frees caller
  *    memory.  Work is ordered on `stream` (a cudaStream_t; NULL = legacy
@@ -55,7 +60,7 @@ enum ec_status {
     EC_OK = 0,
     EC_ERR_ARG = 1,          /* bad dims, L, pointer, descriptor/connectivity combination, unsorted thresholds */
     EC_ERR_DTYPE = 2,        /* unknown dtype, or NULL thresholds with EC_F32 */
-    EC_ERR_UNSUPPORTED = 3,  /* valid request the library does not implement (3D 6-connectivity) */
+    EC_ERR_UNSUPPORTED = 3,  /* valid request the library does not implement (internal: a kernel that does not fit) */
     EC_ERR_OOM = 4,          /* scratch allocation failed, or a memory cap / budget is too small */
     EC_ERR_CUDA = 5,         /* a CUDA runtime call failed; ec_last_error() has its message */
     EC_ERR_TIMEOUT = 6,      /* a bounded device or host wait gave up */
@@ -105,9 +110,15 @@ int ec_ctx_destroy(ec_ctx *ctx);
  *    level-count and size buckets, descriptors) times the candidate plans
  *    (tile depth, grid, schedule) on itself, synchronously, and later
  *    requests of the class use the fastest.  With the environment variable
- *    EC_AUTOTUNE_CACHE naming a file, tuned plans persist there as JSON.   */
+ *    EC_AUTOTUNE_CACHE naming a file, tuned plans persist there as JSON.
+ *  EC_OPT_TEST_GIVE_UP (testing the failure path only): 1 = in the next 3D
+ *    curve requests on the float32 TMA path, every block gives up its first
+ *    bounded device wait at once, as if the staged plane had not arrived in
+ *    time.  The copies already requested still land (the block waits for
+ *    them, bounded) before it returns; the curves read INT64_MIN and, with
+ *    EC_OPT_VALIDATE, the call returns EC_ERR_TIMEOUT.  0 = normal.        */
 enum { EC_OPT_ALGO = 1, EC_OPT_VALIDATE = 2, EC_OPT_TILE_Z = 3, EC_OPT_GRID = 4, EC_OPT_PROFILE = 5,
-       EC_OPT_HIST_SCHEDULE = 6, EC_OPT_AUTOTUNE = 7 };
+       EC_OPT_HIST_SCHEDULE = 6, EC_OPT_AUTOTUNE = 7, EC_OPT_TEST_GIVE_UP = 8 };
 int ec_ctx_set_option(ec_ctx *ctx, int option, int64_t value);
 
 /* The tuned plan of a shape class, if the autotuner has one:
@@ -130,7 +141,7 @@ int ec_curve_2d(ec_ctx *ctx, const void *field_dev, const int64_t dims[2], int d
 
 /* EC / perimeter / area / volume curves of a 3D field resident on the device.
  * Same conventions; dims = {d, h, w}.  Algorithm 3 of the paper (Appendix),
- * Table 2 weights, 26-connectivity.
+ * Table 2 weights; 26-connectivity (or 6, see the conventions above).
  * Performance note (results do not depend on it): float32 fields whose start
  * is 16-byte aligned and whose row length is a multiple of 4 are staged by
  * the tensor memory accelerator; other fields that start 16-byte aligned by
@@ -333,6 +344,12 @@ int ec_type_table(int32_t ndim, int32_t *out);
  * {8*EC, 2*perimeter, 4*area, 8*volume} per 8-bit mask (bit x + 2y + 4z). */
 int ec_vertex_table_2d(int32_t *out);
 int ec_vertex_table_3d(int32_t *out);
+/* 8 * EC per vertex under 3D 6-connectivity, out[256] per 8-bit mask: the
+ * active voxels of the mask, minus 2 per quarter face whose two voxels are
+ * active, plus 4 per half edge whose four voxels are active, minus 8 when all
+ * eight are.  Constant on every vertex type (ec_type_table), so it is also
+ * the 6-connected EC weight row for ec_apply_weights (scale 8). */
+int ec_vertex_table_3d_ec6(int32_t *out);
 /* Exhaustive host check that the per-top-cell closed forms the fast kernels
  * evaluate equal the per-vertex tables regrouped by entering cell, over all
  * 2^8 (2D) and 2^26 (3D) neighbour precedence patterns.  Returns the number

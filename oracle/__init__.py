@@ -51,7 +51,11 @@ def _load():
             lib.oracle_curves_3d.argtypes = [P, I64, I64, I64, I32, P, P, P, P]
             lib.oracle_curves_3d_zrange.argtypes = [P, I64, I64, I64, I32, I64, I64, P, P, P, P]
             lib.oracle_hashbox_u16.argtypes = [ctypes.c_uint64, I64, I64, I64, I64, I64, I64, P]
+            lib.oracle_ec6_3d.argtypes = [P, I64, I64, I64, I32, P]
+            lib.oracle_ec_dual_2d.argtypes = [P, I64, I64, I32, P]
             lib.oracle_num_threads.restype = ctypes.c_int
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = None
             _lib = lib
     return _lib
 
@@ -62,6 +66,12 @@ def _ptr(a):
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads the oracle uses from now on (n < 1: the OpenMP default).  For
+    timing only: results do not depend on it."""
+    _load().oracle_set_threads(int(n))
 
 
 def bin_field(field: np.ndarray, thresholds, L: int) -> np.ndarray:
@@ -116,6 +126,30 @@ def curves_3d_zrange(bins: np.ndarray, L: int, zlo: int, zhi: int) -> dict:
     return out
 
 
+def ec6_3d(bins: np.ndarray, L: int) -> np.ndarray:
+    """EC curve of a binned 3D field under 6-connectivity: cells whose incident
+    voxels are all active, #voxels - #face pairs + #squares - #cubes."""
+    bins = np.ascontiguousarray(bins, dtype=np.int32)
+    d, h, w = bins.shape
+    out = np.zeros(L, dtype=np.int64)
+    rc = _load().oracle_ec6_3d(_ptr(bins), d, h, w, L, _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_ec6_3d failed ({rc})")
+    return out
+
+
+def ec_dual_2d(bins: np.ndarray, L: int) -> np.ndarray:
+    """The same reading in 2D (cells whose incident pixels are all active):
+    #pixels - #edge pairs + #2x2 squares, the 4-connected EC."""
+    bins = np.ascontiguousarray(bins, dtype=np.int32)
+    h, w = bins.shape
+    out = np.zeros(L, dtype=np.int64)
+    rc = _load().oracle_ec_dual_2d(_ptr(bins), h, w, L, _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_ec_dual_2d failed ({rc})")
+    return out
+
+
 EC, PERIMETER, AREA, VOLUME = 1, 2, 4, 8
 
 
@@ -134,6 +168,8 @@ def ec_curves(field: np.ndarray, thresholds, L: int, connectivity: int, descript
             rows.append(c["area"])
     else:
         c = curves_3d(bins, L)
+        if connectivity == 6:
+            c["ec"] = ec6_3d(bins, L)
         for bit, key in ((EC, "ec"), (PERIMETER, "perimeter"), (AREA, "area"), (VOLUME, "volume")):
             if descriptors & bit:
                 rows.append(c[key])

@@ -34,6 +34,19 @@
  *     8-connected complex except that a vertex whose two active pixels touch
  *     only diagonally (type QD) counts as two vertices.  So
  *     chi4_k = chi8_k + #(vertices of type QD at level k).
+ *   - 3D EC under 6-connectivity (the paper fixes 26-connectivity in 3D and
+ *     gives the other connectivity only for 2D, Table 1's 4-C columns; this is
+ *     the reading taken): under face adjacency, cells join the active set
+ *     through shared cells only when every voxel around the shared cell is
+ *     active.  So the complex at level k has a cell exactly when ALL of its
+ *     incident top cells are active (exit = max(bin of incident top cells),
+ *     top cells outside the domain never active), and by the duality between
+ *     this complex and the voxel adjacency structure (voxels, face-adjacent
+ *     pairs, 2x2 squares, 2x2x2 cubes)
+ *         chi6_k = #C - #F + #E - #V   over the cells with exit <= k,
+ *     i.e. #voxels - #face pairs + #squares - #cubes.  The same reading in 2D,
+ *     chi = #F - #E + #V over cells with exit <= k, is the 4-connected EC of
+ *     Table 1 (oracle_ec_dual_2d, used to check this reading).
  *
  * Levels: thresholds t_0 <= ... <= t_{L-1}; bin(x) = min{k : x <= t_k}, or L
  * when x exceeds every threshold (or is NaN).  Bin L is "never active".
@@ -326,6 +339,69 @@ int oracle_curves_3d(const int32_t *bins, int64_t d, int64_t h, int64_t w, int32
     return oracle_curves_3d_zrange(bins, d, h, w, L, 0, 2 * d, ec, perim, area, vol);
 }
 
+/* ------------------------------------------------ 6-connected EC (3D) and
+ * its 2D counterpart: a cell is in the complex when all incident top cells
+ * are active, from the level exit = max(bin of incident top cells); the
+ * curve is the running sum of the counts with sign (-1)^(n - dim). */
+static int ec_dual(const int32_t *bins, int64_t d, int64_t h, int64_t w, int32_t L, int ndim, int64_t *out)
+{
+    if (d < 1 || h < 1 || w < 1 || L < 1) return -1;
+    const int64_t D2 = ndim == 3 ? 2 * d : 0, H2 = 2 * h, W2 = 2 * w, NB = (int64_t)L + 1;
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    int64_t *acc = (int64_t *)calloc((size_t)(NB * nthr), sizeof(int64_t));
+    if (!acc) return -2;
+    #pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        int64_t *sgn = acc + tid * NB;   /* signed cell count per exit level */
+        #pragma omp for schedule(dynamic, 1)
+        for (int64_t Z = 0; Z <= D2; Z++) {
+            int64_t sz[2] = {0, -1}; int nz = 1;
+            if (ndim == 3) nz = axis_slots(Z, d, sz);
+            for (int64_t Y = 0; Y <= H2; Y++) {
+                int64_t sy[2]; int ny = axis_slots(Y, h, sy);
+                for (int64_t X = 0; X <= W2; X++) {
+                    int64_t sx[2]; int nx = axis_slots(X, w, sx);
+                    int32_t ex = -1;
+                    for (int k = 0; k < nz; k++)
+                        for (int j = 0; j < ny; j++)
+                            for (int i = 0; i < nx; i++) {
+                                int32_t v = L;
+                                if (sz[k] >= 0 && sy[j] >= 0 && sx[i] >= 0)
+                                    v = bins[(sz[k] * h + sy[j]) * w + sx[i]];
+                                ex = imax(ex, v);
+                            }
+                    const int dim = (int)(X & 1) + (int)(Y & 1) + (ndim == 3 ? (int)(Z & 1) : 0);
+                    sgn[ex] += ((ndim - dim) & 1) ? -1 : 1;
+                }
+            }
+        }
+    }
+    int64_t run = 0;
+    for (int64_t k = 0; k < L; k++) {
+        for (int t = 0; t < nthr; t++) run += acc[t * NB + k];
+        out[k] = run;
+    }
+    free(acc);
+    return 0;
+}
+
+int oracle_ec6_3d(const int32_t *bins, int64_t d, int64_t h, int64_t w, int32_t L, int64_t *ec6)
+{
+    return ec_dual(bins, d, h, w, L, 3, ec6);
+}
+
+int oracle_ec_dual_2d(const int32_t *bins, int64_t h, int64_t w, int32_t L, int64_t *ec)
+{
+    return ec_dual(bins, 1, h, w, L, 2, ec);
+}
+
 /* ------------------------------------------- hash-box field (workload input)
  *
  * Counter-based generator for the low-memory streaming workload, implemented
@@ -382,6 +458,19 @@ int oracle_hashbox_u16(uint64_t seed, int64_t x0, int64_t y0, int64_t z0,
             }
     free(hh);
     return 0;
+}
+
+/* Threads later calls use (timing the oracle on one core or on all of them;
+ * n < 1 restores the OpenMP default).  Results do not depend on it. */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    static int dflt = 0;
+    if (!dflt) dflt = omp_get_max_threads();
+    omp_set_num_threads(n >= 1 ? n : dflt);
+#else
+    (void)n;
+#endif
 }
 
 int oracle_num_threads(void)

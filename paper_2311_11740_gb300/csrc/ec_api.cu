@@ -203,12 +203,9 @@ int ec::validate_request(int ndim, const void *field, const int64_t *dims, int d
         set_error("2D connectivity must be 8 or 4 (got %d)", connectivity);
         return EC_ERR_ARG;
     }
-    if (ndim == 3) {
-        if (connectivity == 6) {
-            set_error("3D 6-connectivity is not implemented (the paper fixes 26)");
-            return EC_ERR_UNSUPPORTED;
-        }
-        if (connectivity != 26) { set_error("3D connectivity must be 26 (got %d)", connectivity); return EC_ERR_ARG; }
+    if (ndim == 3 && connectivity != 26 && connectivity != 6) {
+        set_error("3D connectivity must be 26 or 6 (got %d)", connectivity);
+        return EC_ERR_ARG;
     }
     if (L > 0 && (!field || !out)) { set_error("field or out is NULL"); return EC_ERR_ARG; }
     return EC_OK;
@@ -242,6 +239,7 @@ int run_curve(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int
     plan.grid = ctx->grid;
     plan.num_sms = ctx->num_sms;
     plan.prof = ctx->profile ? ctx : nullptr;
+    plan.test_give_up = ctx->test_give_up;
     if (ctx->autotune && plan.algo != ALGO_VERTEX) {
         rc = tuned_plan(ctx, ndim, field, dims, dtype, thr, L, connectivity, descriptors, out, s, plan);
         if (rc) return rc;
@@ -278,13 +276,18 @@ int ec::enqueue_curve(const CurvePlan &plan, int ndim, const void *field, const 
     BinArgs ba{L, dtype, thr};
     HistArgs ha{rows, hist, use_smem_hist(rows.nd, L) ? 1 : 0, plan.hist_schedule};
     ha.planar = plan.algo == ALGO_AUTO || plan.algo == ALGO_PLANAR;
+    ha.test_give_up = plan.test_give_up;
     int rc;
     if (plan.prof && (rc = prof_begin(plan.prof, s))) return rc;
     if (ndim == 3) {
+        // 6-connectivity runs on the generic kernels (the EC row from the AND
+        // counterparts of the covers, or the 6-connected vertex table)
+        const int conn6 = connectivity == 6 ? 1 : 0;
         rc = EC_ERR_UNSUPPORTED;
-        if (algo == ALGO_VOXEL) rc = launch_fast_3d(field, dims, ba, ha, plan.tile_z, plan.grid, plan.num_sms, flags, s);
+        if (algo == ALGO_VOXEL && !conn6)
+            rc = launch_fast_3d(field, dims, ba, ha, plan.tile_z, plan.grid, plan.num_sms, flags, s);
         if (rc == EC_ERR_UNSUPPORTED)
-            rc = launch_curve_3d(field, dims, ba, ha, algo, plan.tile_z, plan.grid, plan.num_sms, s);
+            rc = launch_curve_3d(field, dims, ba, ha, algo, plan.tile_z, plan.grid, plan.num_sms, s, nullptr, conn6);
     } else {
         rc = EC_ERR_UNSUPPORTED;
         if (algo == ALGO_VOXEL)
@@ -404,6 +407,7 @@ int ec_ctx_set_option(ec_ctx *ctx, int option, int64_t value)
         if (value < 0 || value > 3) { set_error("bad histogram schedule"); return EC_ERR_ARG; }
         ctx->hist_schedule = (int)value;
         return EC_OK;
+    case EC_OPT_TEST_GIVE_UP: ctx->test_give_up = value ? 1 : 0; return EC_OK;
     case EC_OPT_PROFILE: {
         std::lock_guard<std::mutex> lock(ctx->mu);
         ctx->profile = value ? 1 : 0;
@@ -446,6 +450,14 @@ int ec_vertex_table_2d(int32_t *out)
     return EC_OK;
 }
 
+int ec_vertex_table_3d_ec6(int32_t *out)
+{
+    static constexpr Table3D6 t6 = make_table_3d_ec6();
+    if (!out) return EC_ERR_ARG;
+    memcpy(out, t6.v, sizeof(t6.v));
+    return EC_OK;
+}
+
 int ec_vertex_table_3d(int32_t *out)
 {
     if (!out) return EC_ERR_ARG;
@@ -457,6 +469,7 @@ int64_t ec_selfcheck_rules(void)
 {
     const Table2D &t2 = host_table_2d();
     const Table3D &t3 = host_table_3d();
+    static constexpr Table3D6 t6 = make_table_3d_ec6();
     int64_t bad = 0;
     // 2D: all 2^8 precedence patterns of the 8 neighbours
     for (uint32_t i = 0; i < 256; i++) {
@@ -502,6 +515,17 @@ int64_t ec_selfcheck_rules(void)
                 }
                 const Delta3 d = voxel_delta_3d(P);
                 if (s0 != 8 * d.ec || s1 != 2 * d.per || s2 != 4 * d.area || s3 != 8) b++;
+                // 6-connectivity: the same telescoping with the 6-connected table
+                int s6 = 0;
+                for (int v = 0; v < 8; v++) {
+                    const int vx = v & 1, vy = (v >> 1) & 1, vz = v >> 2;
+                    const uint32_t q = P >> (vx + 3 * vy + 9 * vz);
+                    const unsigned m = (q & 3u) | (((q >> 3) & 3u) << 2) | (((q >> 9) & 3u) << 4) |
+                                       (((q >> 12) & 3u) << 6);
+                    const unsigned cbit = (unsigned)((1 - vx) + 2 * (1 - vy) + 4 * (1 - vz));
+                    s6 += t6.v[m | (1u << cbit)] - t6.v[m];
+                }
+                if (s6 != 8 * voxel_delta_3d6(P)) b++;
             }
             part[t] = b;
         });

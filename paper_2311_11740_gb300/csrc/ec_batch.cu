@@ -440,12 +440,12 @@ extern "C" int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, voi
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return vox(a) > vox(b); });
     std::vector<BField> bf;
     std::vector<BItem> items;
-    std::vector<int> separate;   // 3D fields with more levels than 16-bit comparison lanes hold
+    std::vector<int> separate;   // 3D fields with more levels than 16-bit comparison lanes hold, or 6-connected
     size_t hist_entries = 0, max_smem_entries = 0;
     for (int oi = 0; oi < n; oi++) {
         const ec_field_desc &d = fields[order[oi]];
         if (d.L == 0) continue;
-        if (d.ndim == 3 && d.L > kMaxFastL3) {
+        if (d.ndim == 3 && (d.L > kMaxFastL3 || d.connectivity == 6)) {
             separate.push_back(order[oi]);
             continue;
         }

@@ -54,12 +54,15 @@ struct HistArgs {
     int smem_hist;      // 1: block-private shared-memory int32 histogram, flushed at the end
     int schedule = 0;   // shared-memory update schedule: 0 auto, 1 one atomic per voxel, 2 warp-aggregated
     int planar = 0;     // 3D per-voxel kernels: count with the planar form (ec_slice.h) where it applies
+    int test_give_up = 0;   // testing: every block gives up its first bounded wait (EC_OPT_TEST_GIVE_UP)
 };
 
 // Launch helpers implemented in ec_kernels.cu.  All are stream-ordered and
 // return EC_OK or an error status.
+// conn6 = 1: the EC row under 6-connectivity (voxel_delta_3d6 / Table3D6).
 int launch_curve_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha,
-                    int algo, int tile_z, int grid, int num_sms, cudaStream_t s, const int zrange[4] = nullptr);
+                    int algo, int tile_z, int grid, int num_sms, cudaStream_t s, const int zrange[4] = nullptr,
+                    int conn6 = 0);
 int launch_curve_2d(const void *field, const int64_t dims[2], const BinArgs &ba, const HistArgs &ha,
                     int connectivity, int algo, int grid, int num_sms, cudaStream_t s);
 // The fast per-voxel 3D kernel (TMA staging, paired comparisons).  Returns
@@ -135,6 +138,7 @@ struct ec_ctx {
     void *tune_cache = nullptr;             // autotuned plans per shape class
     void *stream_state = nullptr;           // streaming buffers, streams and events
     int autotune = 0;
+    int test_give_up = 0;
     std::mutex mu;
 };
 
@@ -147,6 +151,7 @@ struct CurvePlan {
     int grid = 0;
     int num_sms = 1;
     ec_ctx *prof = nullptr;   // bracket the histogram kernel with this context's events
+    int test_give_up = 0;     // EC_OPT_TEST_GIVE_UP
 };
 // Scratch bytes of one curve request (flags + int64 histogram).
 size_t curve_scratch_bytes(uint32_t descriptors, int32_t L);

@@ -23,6 +23,7 @@ namespace ec {
 
 __constant__ Table2D c_tab2 = make_table_2d();
 __constant__ Table3D c_tab3 = make_table_3d();
+__constant__ Table3D6 c_tab3e6 = make_table_3d_ec6();
 
 constexpr int kThreads = 256;
 constexpr int kSmemThrMax = 4096;   // thresholds live in shared memory up to this many levels
@@ -180,7 +181,8 @@ __device__ __forceinline__ void stage_plane3(uint16_t *slot, const T *__restrict
 
 // Per-voxel regrouped path: one histogram update per voxel at its own level.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_voxel3d(const T *__restrict__ f, Geom3 g, BinArgs ba, HistArgs ha)
+__global__ void __launch_bounds__(kThreads) k_voxel3d(const T *__restrict__ f, Geom3 g, BinArgs ba, HistArgs ha,
+                                                      int conn6)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const size_t hb = hist_smem_bytes(ha, ba.L);
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(kThreads) k_voxel3d(const T *__restrict__ f, G
                         }
                 }
                 const Delta3 d = voxel_delta_3d(P);
-                hist.add(0, kc, d.ec);
+                hist.add(0, kc, conn6 ? voxel_delta_3d6(P) : d.ec);
                 hist.add(1, kc, d.per);
                 hist.add(2, kc, d.area);
                 hist.add(3, kc, 1);
@@ -255,7 +257,8 @@ __device__ __forceinline__ void sort8(uint32_t s[8])
 // the vertex's 8 (level, position) keys, then walk the prefixes of the sorted
 // order; the vertex type changes from T[m] to T[m | bit] at each value.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_vertex3d(const T *__restrict__ f, Geom3 g, BinArgs ba, HistArgs ha)
+__global__ void __launch_bounds__(kThreads) k_vertex3d(const T *__restrict__ f, Geom3 g, BinArgs ba, HistArgs ha,
+                                                       int conn6)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const size_t hb = hist_smem_bytes(ha, ba.L);
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(kThreads) k_vertex3d(const T *__restrict__ f, 
     Binner<T> bin = make_binner<T>(ba, smem + hb);
     int4 *tab = (int4 *)(smem + hb + bb);
     for (int i = threadIdx.x; i < 256; i += blockDim.x)
-        tab[i] = make_int4(c_tab3.v[i][0], c_tab3.v[i][1], c_tab3.v[i][2], c_tab3.v[i][3]);
+        tab[i] = make_int4(conn6 ? c_tab3e6.v[i] : c_tab3.v[i][0], c_tab3.v[i][1], c_tab3.v[i][2], c_tab3.v[i][3]);
     uint16_t *ring = (uint16_t *)(smem + hb + bb + 256 * sizeof(int4));
     const uint32_t L = (uint32_t)ba.L;
     const int tx = threadIdx.x % TX3, ty = threadIdx.x / TX3;
@@ -525,7 +528,8 @@ static int prepare_kernel(KernelT kernel, size_t smem, int num_sms, int items, i
 
 template <typename T>
 static int launch3(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha,
-                   int algo, int tile_z, int grid_override, int num_sms, cudaStream_t s, const int zrange[4])
+                   int algo, int tile_z, int grid_override, int num_sms, cudaStream_t s, const int zrange[4],
+                   int conn6)
 {
     Geom3 g;
     g.D = dims[0]; g.H = dims[1]; g.W = dims[2];
@@ -550,23 +554,23 @@ static int launch3(const void *field, const int64_t dims[3], const BinArgs &ba, 
     if (vertex) {
         int rc = prepare_kernel(k_vertex3d<T>, smem, num_sms, items, grid_override, &grid);
         if (rc) return rc;
-        k_vertex3d<T><<<grid, kThreads, smem, s>>>((const T *)field, g, ba, ha);
+        k_vertex3d<T><<<grid, kThreads, smem, s>>>((const T *)field, g, ba, ha, conn6);
     } else {
         int rc = prepare_kernel(k_voxel3d<T>, smem, num_sms, items, grid_override, &grid);
         if (rc) return rc;
-        k_voxel3d<T><<<grid, kThreads, smem, s>>>((const T *)field, g, ba, ha);
+        k_voxel3d<T><<<grid, kThreads, smem, s>>>((const T *)field, g, ba, ha, conn6);
     }
     EC_CUDA(cudaGetLastError());
     return EC_OK;
 }
 
 int launch_curve_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha,
-                    int algo, int tile_z, int grid, int num_sms, cudaStream_t s, const int zrange[4])
+                    int algo, int tile_z, int grid, int num_sms, cudaStream_t s, const int zrange[4], int conn6)
 {
     switch (ba.dtype) {
-    case EC_U8: return launch3<uint8_t>(field, dims, ba, ha, algo, tile_z, grid, num_sms, s, zrange);
-    case EC_U16: return launch3<uint16_t>(field, dims, ba, ha, algo, tile_z, grid, num_sms, s, zrange);
-    case EC_F32: return launch3<float>(field, dims, ba, ha, algo, tile_z, grid, num_sms, s, zrange);
+    case EC_U8: return launch3<uint8_t>(field, dims, ba, ha, algo, tile_z, grid, num_sms, s, zrange, conn6);
+    case EC_U16: return launch3<uint16_t>(field, dims, ba, ha, algo, tile_z, grid, num_sms, s, zrange, conn6);
+    case EC_F32: return launch3<float>(field, dims, ba, ha, algo, tile_z, grid, num_sms, s, zrange, conn6);
     }
     set_error("unknown dtype %d", ba.dtype);
     return EC_ERR_DTYPE;

@@ -82,6 +82,7 @@ struct Params {
     int rows[kMaxDesc];
     int *err;              // bit 2: a bounded wait gave up
     const int *uni;        // [0] = 1 if the uniform-spacing guess is exact, [1], [2] = its scale and offset
+    int test_give_up;      // testing: give up the first bounded wait of every block
 };
 
 struct Ctx {
@@ -97,6 +98,7 @@ struct Ctx {
     uint32_t base;             // ring sequence number of plane z0 - 1
     uint32_t parity;
     uint32_t inflight;         // thread 0: ring slots with a TMA copy issued and not yet waited for
+    int give_up;               // thread 0, testing: treat the next wait as timed out
 };
 
 __device__ __forceinline__ uint32_t slot_of(const Ctx &c, int plane) { return (c.base + (uint32_t)(plane - (c.z0 - 1))) % NS; }
@@ -168,7 +170,11 @@ __device__ __forceinline__ bool barrier_step(Ctx &c, const CUtensorMap *tmap, in
             const int pb = h + q;
             if (pb > c.z1) break;
             const uint32_t s = slot_of(c, pb);
-            if (!fast3d::mbar_wait(&c.bars[s], (c.parity >> s) & 1u)) {
+            // (testing) a wait given up at once leaves the copy in flight and
+            // its phase unconsumed: the drain below waits for it
+            const bool arrived = c.give_up ? false : fast3d::mbar_wait(&c.bars[s], (c.parity >> s) & 1u);
+            c.give_up = 0;
+            if (!arrived) {
                 *c.abort_flag = 1;
                 atomicOr(c.err, 4);
                 break;
@@ -319,6 +325,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_planar3d(const __grid_constant_
     c.left1 = left_share(threadIdx.x + kThreads);
     c.parity = 0;
     c.inflight = 0;
+    c.give_up = p.test_give_up;
     c.zv0 = p.zv0;
     c.zv1 = p.zv1;
     uint32_t seq = 0;
@@ -458,6 +465,7 @@ int launch_planar_3d(const void *field, const int64_t dims[3], const BinArgs &ba
     for (int i = 0; i < kMaxDesc; i++) p.rows[i] = ha.rows.row[i];
     p.err = err_flag;
     p.uni = err_flag + 2;
+    p.test_give_up = ha.test_give_up;
     CUtensorMap map;
     memset(&map, 0, sizeof map);
     cuuint64_t gdim[3] = {(cuuint64_t)p.W, (cuuint64_t)p.H, (cuuint64_t)p.D};

@@ -130,6 +130,40 @@ constexpr Table3D make_table_3d()
     return t;
 }
 
+// 3D EC under 6-connectivity, per vertex, scaled by 8.  Under face adjacency
+// a cell of the grid belongs to the complex exactly when ALL its incident
+// voxels are active (the dual of the closed complex above, whose cells need
+// only one), and chi6 = #voxels - #cells of dimension 2 + #dim 1 - #dim 0
+// counted over those cells.  A vertex owns 1/8 of each incident voxel, 1/4 of
+// each incident face, 1/2 of each incident edge and itself.
+struct Table3D6 { int32_t v[256]; };
+
+constexpr Table3D6 make_table_3d_ec6()
+{
+    Table3D6 t{};
+    for (unsigned m = 0; m < 256; m++) {
+        int faces = 0, edges = 0;
+        for (int axis = 0; axis < 3; axis++) {
+            const int a1 = (axis + 1) % 3, a2 = (axis + 2) % 3;
+            // quarter faces normal to `axis`: both voxels of the pair active
+            for (unsigned s1 = 0; s1 < 2; s1++)
+                for (unsigned s2 = 0; s2 < 2; s2++) {
+                    const unsigned b0 = (s1 << a1) | (s2 << a2), b1 = b0 | (1u << axis);
+                    faces += ((m >> b0) & 1u) && ((m >> b1) & 1u) ? 1 : 0;
+                }
+            // half edges along `axis`: all four voxels on that side active
+            for (unsigned side = 0; side < 2; side++) {
+                bool all = true;
+                for (unsigned b = 0; b < 8; b++)
+                    if (((b >> axis) & 1u) == side && !((m >> b) & 1u)) all = false;
+                edges += all ? 1 : 0;
+            }
+        }
+        t.v[m] = popc_c(m) - 2 * faces + 4 * edges - (m == 0xFFu ? 8 : 0);
+    }
+    return t;
+}
+
 // ------------------------------------------------- per-top-cell closed forms
 
 // 3D: P holds one bit per neighbour n of the entering voxel c, set when n
@@ -186,6 +220,32 @@ EC_HD Delta3 voxel_delta_3d(uint32_t P)
     d.per = 12 - 2 * nM;
     d.area = 6 - 2 * nF;
     return d;
+}
+
+// 3D EC change under 6-connectivity when voxel c enters (P as above): c
+// brings itself (+1), completes each face whose neighbour precedes (-1), each
+// edge all 3 of whose other voxels precede (+1) and each corner all 7 of
+// whose other voxels precede (-1): the AND counterparts of the covers above.
+EC_HD int voxel_delta_3d6(uint32_t P)
+{
+    const int nF = popc32(P & kFaceMask3);
+    // corner blocks: AND over each 2x2x2 block with c's own bit set
+    const uint32_t Pc = P | (1u << 13);
+    const uint32_t w1 = Pc & (Pc >> 1), w2 = w1 & (w1 >> 3), w3 = w2 & (w2 >> 9);
+    const int nV = popc32(w3 & kCornerOrigins3);
+    // edges: the edge neighbour d and its two face neighbours, aligned at d's
+    // bit as in voxel_delta_3d
+    const uint32_t Pr1 = P >> 1, Pl1 = P << 1, Pr3 = P >> 3, Pl3 = P << 3, Pr9 = P >> 9, Pl9 = P << 9;
+    const uint32_t dy_lo_z = (1u << 9) | (1u << 11), dy_hi_z = (1u << 15) | (1u << 17);
+    const uint32_t dz_lo = (1u << 1) | (1u << 7) | (1u << 3) | (1u << 5);
+    const uint32_t dz_hi = (1u << 19) | (1u << 25) | (1u << 21) | (1u << 23);
+    const uint32_t A1 = (Pr3 & dy_lo_z) | (Pl3 & dy_hi_z) | (Pr9 & dz_lo) | (Pl9 & dz_hi);
+    const uint32_t dx_lo = (1u << 9) | (1u << 15) | (1u << 3) | (1u << 21);
+    const uint32_t dx_hi = (1u << 11) | (1u << 17) | (1u << 5) | (1u << 23);
+    const uint32_t dy_lo_x = (1u << 1) | (1u << 19), dy_hi_x = (1u << 7) | (1u << 25);
+    const uint32_t A2 = (Pr1 & dx_lo) | (Pl1 & dx_hi) | (Pr3 & dy_lo_x) | (Pl3 & dy_hi_x);
+    const int nE = popc32(A1 & A2 & P & kEdgeMask3);
+    return 1 - nF + nE - nV;
 }
 
 // 2D: P bit (dx+1) + 3*(dy+1), centre bit 4 zero.  Changes of EC under 8-

@@ -181,9 +181,12 @@ extern "C" int ec_curve_3d_stream(ec_ctx *ctx, const void *host_field, ec_slab_f
         const int64_t bdims[3] = {n + 2, h, w};
         const int zr[4] = {1, (int)(n + 1), z0 == 0 ? 1 : 0, z1 == d ? (int)(n + 1) : (int)(n + 2)};
         if (ctx->profile && (rc = prof_begin(ctx, res.comp))) return rc;
-        rc = launch_fast_3d(buf, bdims, ba, ha, ctx->tile_z, ctx->grid, ctx->num_sms, flags, res.comp, zr);
+        rc = EC_ERR_UNSUPPORTED;
+        if (connectivity != 6)
+            rc = launch_fast_3d(buf, bdims, ba, ha, ctx->tile_z, ctx->grid, ctx->num_sms, flags, res.comp, zr);
         if (rc == EC_ERR_UNSUPPORTED)
-            rc = launch_curve_3d(buf, bdims, ba, ha, ALGO_VOXEL, ctx->tile_z, ctx->grid, ctx->num_sms, res.comp, zr);
+            rc = launch_curve_3d(buf, bdims, ba, ha, ALGO_VOXEL, ctx->tile_z, ctx->grid, ctx->num_sms, res.comp, zr,
+                                 connectivity == 6 ? 1 : 0);
         if (rc) return rc;
         if (ctx->profile && (rc = prof_end(ctx, res.comp))) return rc;
         EC_CUDA(cudaEventRecord(res.freed[b], res.comp));

@@ -19,6 +19,7 @@ EC_U8, EC_U16, EC_F32 = 0, 1, 2
 EC_DESC_EC, EC_DESC_PERIMETER, EC_DESC_AREA, EC_DESC_VOLUME = 1, 2, 4, 8
 EC_OPT_ALGO, EC_OPT_VALIDATE, EC_OPT_TILE_Z, EC_OPT_GRID, EC_OPT_PROFILE, EC_OPT_HIST_SCHEDULE = 1, 2, 3, 4, 5, 6
 EC_OPT_AUTOTUNE = 7
+EC_OPT_TEST_GIVE_UP = 8
 ALGO_AUTO, ALGO_VOXEL, ALGO_VERTEX, ALGO_PLANAR = 0, 1, 2, 3
 STATUS = {0: "EC_OK", 1: "EC_ERR_ARG", 2: "EC_ERR_DTYPE", 3: "EC_ERR_UNSUPPORTED", 4: "EC_ERR_OOM",
           5: "EC_ERR_CUDA", 6: "EC_ERR_TIMEOUT", 7: "EC_ERR_OVERFLOW", 8: "EC_ERR_BUSY"}
@@ -68,6 +69,7 @@ def lib():
             L.ec_workspace_bytes.restype = ctypes.c_size_t
             L.ec_vertex_table_2d.argtypes = [P]
             L.ec_vertex_table_3d.argtypes = [P]
+            L.ec_vertex_table_3d_ec6.argtypes = [P]
             L.ec_selfcheck_rules.restype = I64
             L.ec_server_create.argtypes = [P, ctypes.c_size_t, I32, ctypes.POINTER(P)]
             L.ec_server_submit.argtypes = [P, ctypes.POINTER(FieldDesc), ctypes.POINTER(ctypes.c_uint64)]
@@ -491,6 +493,13 @@ def vertex_table_2d() -> np.ndarray:
 def vertex_table_3d() -> np.ndarray:
     out = np.zeros((256, 4), np.int32)
     _check(lib().ec_vertex_table_3d(out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def vertex_table_3d_ec6() -> np.ndarray:
+    """8 * EC per 8-bit vertex mask under 3D 6-connectivity (int32 [256])."""
+    out = np.zeros(256, dtype=np.int32)
+    _check(lib().ec_vertex_table_3d_ec6(out.ctypes.data_as(ctypes.c_void_p)))
     return out
 
 

@@ -276,12 +276,62 @@ def test_config1_full(ctx):
         check(ctx, f, None, 256, conn=conn)
 
 
+# 3D 6-connectivity: every per-voxel and per-vertex path against the oracle's
+# reading (cells whose incident voxels are all active); the other descriptors
+# do not depend on it.
+SHAPES3_C6 = [(1, 1, 1), (2, 3, 5), (7, 11, 13), (33, 9, 31), (5, 64, 65), (16, 40, 68), (70, 3, 8)]
+
+
+@pytest.mark.parametrize("shape", SHAPES3_C6)
+@pytest.mark.parametrize("dtype", ["u8", "u16", "f32"])
+def test_random_3d_6_connectivity(ctx, shape, dtype):
+    rng = np.random.default_rng(zlib.crc32(repr((shape, dtype, "c6")).encode()))
+    if dtype == "u8":
+        L = int(rng.integers(1, 40))
+        f = rng.integers(0, L + 3, size=shape).astype(np.uint8)
+        thr = None
+    elif dtype == "u16":
+        L = int(rng.integers(1, 3000))
+        f = rng.integers(0, L + 50, size=shape).astype(np.uint16)
+        thr = None
+    else:
+        L = int(rng.integers(1, 200))
+        f = workloads.grf_nd(int(rng.integers(1 << 30)), shape, 1.2).numpy().astype(np.float32)
+        thr = np.sort(rng.normal(size=L) * f.std() + f.mean()).astype(np.float32)
+    for desc in (1, 15):
+        check(ctx, f, thr, L, conn=6, desc=desc)
+
+
+def test_exhaustive_binary_2x2x2_6_connectivity(ctx):
+    for bits in range(1 << 8):
+        a = np.array([(bits >> i) & 1 for i in range(8)], np.uint8).reshape(2, 2, 2)
+        check(ctx, a, None, 1, conn=6)
+
+
+def test_6_connectivity_streamed_and_batched(ctx):
+    f, thr = workloads.config3(n=36, nblobs=12, L=90)
+    fh, th = f.numpy(), thr.numpy()
+    want = oracle.ec_curves(fh, th, 90, 6, ALL3)
+    for slab in (1, 7, 64):
+        got = ec.curve_3d_stream(fh, thresholds=th, connectivity=6, descriptors=ALL3, slab_planes=slab, ctx=ctx)
+        np.testing.assert_array_equal(got, want)
+    g = np.random.default_rng(3).integers(0, 20, size=(9, 10, 11)).astype(np.uint8)
+    items = [dict(field=to_dev(fh), thresholds=to_dev(th), L=90, connectivity=6, descriptors=ALL3),
+             dict(field=to_dev(g), thresholds=None, L=20, connectivity=26, descriptors=1),
+             dict(field=to_dev(g), thresholds=None, L=20, connectivity=6, descriptors=9)]
+    outs = ec.batch(items, ctx=ctx)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(outs[0].cpu().numpy(), want)
+    np.testing.assert_array_equal(outs[1].cpu().numpy(), oracle.ec_curves(g, None, 20, 26, 1))
+    np.testing.assert_array_equal(outs[2].cpu().numpy(), oracle.ec_curves(g, None, 20, 6, 9))
+
+
 def test_argument_errors(ctx):
     f = torch.zeros((4, 4, 4), dtype=torch.float32, device="cuda")
     t = torch.zeros(3, dtype=torch.float32, device="cuda")
     with pytest.raises(ec.ECError) as e:
-        ec.curve(f, t, connectivity=6, ctx=ctx)
-    assert e.value.status == 3
+        ec.curve(f, t, connectivity=5, ctx=ctx)
+    assert e.value.status == 1
     with pytest.raises(ec.ECError) as e:
         ec.curve(f, t, connectivity=8, ctx=ctx)
     assert e.value.status == 1

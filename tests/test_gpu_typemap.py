@@ -157,6 +157,19 @@ def test_weights_give_the_curves_3d(ctx):
     np.testing.assert_array_equal(got, tm.apply_weights(counts.cpu().numpy(), W, sc))
 
 
+def test_6_connected_weight_row_gives_the_6_connected_curve(ctx):
+    """The library's 6-connected vertex table, taken per type, weights the
+    type map into the 6-connected EC curve (the connectivity changes only the
+    weights)."""
+    rng = np.random.default_rng(18)
+    f, thr = rand_field(rng, (26, 21, 33), "f32", 40)
+    counts = ec.type_map(to_dev(f), to_dev(thr), ctx=ctx)
+    tt, t6 = ec.type_table(3), ec.vertex_table_3d_ec6()
+    W = np.array([[int(t6[int(np.flatnonzero(tt == t)[0])]) for t in range(ec.NTYPES[3])]], np.int32)
+    got = ec.apply_weights(counts, W, [8], ctx=ctx).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle.ec_curves(f, thr, 40, 6, 1))
+
+
 def test_weights_give_the_curves_2d_both_connectivities(ctx):
     rng = np.random.default_rng(19)
     f, _ = rand_field(rng, (90, 333), "u8", 40)

@@ -105,3 +105,28 @@ def test_bench_type_weights_are_table2_columns(libec):
     want = np.array([[int(8 * r["EC"]) for r in rows], [int(2 * r["Perim"]) for r in rows],
                      [int(4 * r["AreaUsed"]) for r in rows], [int(8 * r["Volume"]) for r in rows]])
     np.testing.assert_array_equal(W, want)
+
+
+def test_vertex_table_3d_ec6_sums_to_the_oracle_and_is_constant_per_type(libec):
+    """The 6-connected per-vertex EC table: summed over every vertex of random
+    binary fields it gives 8 x the oracle's 6-connected EC, and it is constant
+    on each vertex type (so it serves as an ec_apply_weights row)."""
+    import oracle
+    from paper_2311_11740_gb300 import ec
+    t6 = ec.vertex_table_3d_ec6()
+    types = ec.type_table(3)
+    for ty in range(int(types.max()) + 1):
+        assert len(set(t6[types == ty].tolist())) == 1, ty
+    rng = np.random.default_rng(66)
+    for trial in range(60):
+        shape = tuple(int(v) for v in rng.integers(1, 7, size=3))
+        a = (rng.random(shape) < rng.uniform(0.2, 0.9)).astype(np.int64)
+        p = np.zeros(tuple(s + 2 for s in shape), np.int64)
+        p[1:-1, 1:-1, 1:-1] = a
+        d, h, w = p.shape
+        masks = np.zeros((d - 1, h - 1, w - 1), np.int64)
+        for b in range(8):
+            dx, dy, dz = b & 1, (b >> 1) & 1, b >> 2
+            masks |= p[dz:dz + d - 1, dy:dy + h - 1, dx:dx + w - 1] << b
+        want = int(oracle.ec6_3d(np.where(a.astype(bool), 0, 1).astype(np.int32), 1)[0])
+        assert int(t6[masks].sum()) == 8 * want, trial
