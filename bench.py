@@ -13,9 +13,10 @@ sensor frames of 36 small tiles served one frame at a time, and the 2048^3
 low-memory workload streamed from its on-device generator under a 4 GB cap.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-  python bench.py --profile-case [typemap]   (the curve kernel, or the type
-                                      map, alone on a 256 x 512 x 512 slab of
-                                      the field, for ncu captures)
+  python bench.py --profile-case [typemap|2d]   (the curve kernel, or the
+                                      type map, alone on a 256 x 512 x 512 slab
+                                      of the field; or the 2D kernel on the
+                                      16384^2 uint8 field; for ncu captures)
 
 --impl reference times the CPU oracle (the plain cell-counting reference) on
 this machine's host cores, on a bounded sample of the same workload.
@@ -559,8 +560,9 @@ def main():
     ap.add_argument("--batch-requests", type=int, default=256)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-type-map", action="store_true")
-    ap.add_argument("--profile-case", nargs="?", const="curve", choices=("curve", "typemap"),
-                    help="run two curve requests (or two type maps) on the first 256 planes of the field and exit")
+    ap.add_argument("--profile-case", nargs="?", const="curve", choices=("curve", "typemap", "2d"),
+                    help="run two curve requests (or two type maps) on the first 256 planes of the field, or "
+                         "two 2D requests on the 16384^2 uint8 field (2d), and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -578,6 +580,16 @@ def main():
         dist.init_process_group("nccl")
     from paper_2311_11740_gb300 import ec, workloads
 
+    if args.profile_case == "2d":
+        u8, _, _ = workloads.config2(device="cuda")
+        ctx = ec.Context(local)
+        desc2 = ec.EC_DESC_EC | ec.EC_DESC_PERIMETER | ec.EC_DESC_AREA
+        for _ in range(2):
+            res = ec.curve(u8, None, L=256, descriptors=desc2, ctx=ctx)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "16384^2 uint8 smoothed GRF, 256 levels, EC+perimeter+area",
+                          "area_at_top": int(res[2, -1])}))
+        return 0
     n = args.small or N
     field, thr = workloads.config3(device="cuda", n=n) if args.small else workloads.config3(device="cuda")
     if args.profile_case:
