@@ -291,6 +291,36 @@ int ec_curve_3d_file(ec_ctx *ctx, const char *path, int64_t offset, const int64_
                      const void *thresholds_host, int32_t L, int connectivity, uint32_t descriptors,
                      int64_t slab_planes, size_t device_mem_cap, int64_t *out_host);
 
+/* ------------------------------------------------------------ BMP input
+ * The paper's experiments read their images as BMP files (Sec. 2.3, Table 5).
+ * Accepted: uncompressed Windows bitmaps (BITMAPINFOHEADER or later), 8 bits
+ * per pixel with a grayscale palette (R = G = B in every entry; a pixel's
+ * value is its entry's gray level) or 24 / 32 bits per pixel whose pixels all
+ * have R = G = B; rows bottom-up (positive height) or top-down (negative),
+ * padded to 4 bytes.  The field is uint8 with row 0 = the image's top row.
+ * Errors: EC_ERR_ARG (cannot open, truncated, not a BMP, slices of different
+ * sizes), EC_ERR_DTYPE (compressed, other bit depths, colour pixels). */
+
+/* Read a BMP: dims_out = {h, w}; with pixels_host non-NULL also its h*w
+ * pixels (caller's buffer).  Host only; no device or context needed. */
+int ec_bmp_read(const char *path, int64_t dims_out[2], uint8_t *pixels_host);
+
+/* 2D curves of one BMP image (as ec_curve_2d with dtype EC_U8; thresholds
+ * uint8 on the host or NULL for identity levels; out_host int64
+ * [popcount(descriptors)][L] on the host, written before return).  Allocates
+ * and frees the device copy of the image itself; synchronous. */
+int ec_curve_2d_bmp(ec_ctx *ctx, const char *path, const void *thresholds_host, int32_t L, int connectivity,
+                    uint32_t descriptors, int64_t *out_host);
+
+/* 3D curves of a stack of BMP slices, paths[z] = the plane z (all of one
+ * size), streamed through ec_curve_3d_stream: slabs of slab_planes planes are
+ * read into page-locked staging while the GPU counts the previous slab, with
+ * at most device_mem_cap bytes of device memory in use (0 = no cap).  The
+ * volume is never resident as a whole.  Synchronous; out_host as above. */
+int ec_curve_3d_bmp(ec_ctx *ctx, const char *const *paths, int64_t nslices, const void *thresholds_host,
+                    int32_t L, int connectivity, uint32_t descriptors, int64_t slab_planes, size_t device_mem_cap,
+                    int64_t *out_host);
+
 /* ----------------------------------------------- contribution-type map
  * The paper's full output (Sec. 2, Algorithm 1 and Table 1; Sec. 2.2,
  * Algorithm 3 and Table 2; Sec. 4): how many grid vertices have each

@@ -9,10 +9,11 @@
 // Steele, Lea and Flood's published finaliser (OOPSLA 2014).  The field is
 // defined for every integer coordinate, so any sub-box can be generated.
 //
-// One block produces a 32 x 8 column of outputs and walks it along z: per
-// input plane it hashes the 36 x 12 neighbourhood into shared memory, sums
-// 5-wide along x then y, and keeps the last five 2D sums in registers for
-// the sum along z.
+// One block produces a 64 x 32 column of outputs and walks it along z.  Per
+// input plane: the 68 x 36 hashes of its neighbourhood go to shared memory
+// (1.2 hashes per output), 5-wide sums along x are formed four at a time as
+// running sums, and each thread sums 5 rows of those for its 4 x 2 outputs
+// and keeps the last five such plane sums in registers for the sum along z.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,7 +21,7 @@
 
 namespace {
 
-constexpr int GX = 32, GY = 8, HX = GX + 4, HY = GY + 4;
+constexpr int GX = 64, GY = 32, HX = GX + 4, HY = GY + 4;
 
 __device__ __forceinline__ uint32_t hash16(uint64_t seed, int64_t x, int64_t y, int64_t z)
 {
@@ -36,11 +37,15 @@ __device__ __forceinline__ uint32_t hash16(uint64_t seed, int64_t x, int64_t y, 
 __global__ void __launch_bounds__(256) k_hashbox(uint64_t seed, int64_t ox, int64_t oy, int64_t oz, int64_t nx,
                                                  int64_t ny, int64_t nz, uint16_t *__restrict__ dst)
 {
-    __shared__ uint32_t hs[HY][HX];
-    __shared__ uint32_t xs[HY][GX];
-    const int tx = threadIdx.x % GX, ty = threadIdx.x / GX;
+    __shared__ __align__(16) uint32_t hs[HY][HX];   // hashes of the plane's neighbourhood
+    __shared__ __align__(16) uint32_t xs[HY][GX];   // 5-wide sums along x
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // outputs x 4tx .. 4tx+3, y 2ty, 2ty+1
     const int64_t bx0 = (int64_t)blockIdx.x * GX, by0 = (int64_t)blockIdx.y * GY;
-    uint32_t ring[5] = {0, 0, 0, 0, 0};
+    uint32_t ring[5][8];
+#pragma unroll
+    for (int a = 0; a < 5; a++)
+#pragma unroll
+        for (int b = 0; b < 8; b++) ring[a][b] = 0;
     for (int64_t k = -2; k < nz + 2; k++) {
         const int64_t z = oz + k;
         for (int i = threadIdx.x; i < HX * HY; i += blockDim.x) {
@@ -48,22 +53,52 @@ __global__ void __launch_bounds__(256) k_hashbox(uint64_t seed, int64_t ox, int6
             hs[ly][lx] = hash16(seed, ox + bx0 - 2 + lx, oy + by0 - 2 + ly, z);
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < HY * GX; i += blockDim.x) {
-            const int ly = i / GX, lx = i - ly * GX;
-            xs[ly][lx] = hs[ly][lx] + hs[ly][lx + 1] + hs[ly][lx + 2] + hs[ly][lx + 3] + hs[ly][lx + 4];
+        for (int i = threadIdx.x; i < HY * (GX / 4); i += blockDim.x) {
+            const int ly = i >> 4, q = i & 15;
+            const uint4 a = *(const uint4 *)&hs[ly][4 * q], b = *(const uint4 *)&hs[ly][4 * q + 4];
+            uint4 o;
+            o.x = a.x + a.y + a.z + a.w + b.x;
+            o.y = o.x - a.x + b.y;
+            o.z = o.y - a.y + b.z;
+            o.w = o.z - a.z + b.w;
+            *(uint4 *)&xs[ly][4 * q] = o;
         }
         __syncthreads();
-        const uint32_t s2 = xs[ty][tx] + xs[ty + 1][tx] + xs[ty + 2][tx] + xs[ty + 3][tx] + xs[ty + 4][tx];
-        ring[0] = ring[1]; ring[1] = ring[2]; ring[2] = ring[3]; ring[3] = ring[4]; ring[4] = s2;
+        uint4 r[6];
+#pragma unroll
+        for (int j = 0; j < 6; j++) r[j] = *(const uint4 *)&xs[2 * ty + j][4 * tx];
+        uint32_t s[8];
+        s[0] = r[0].x + r[1].x + r[2].x + r[3].x + r[4].x;
+        s[1] = r[0].y + r[1].y + r[2].y + r[3].y + r[4].y;
+        s[2] = r[0].z + r[1].z + r[2].z + r[3].z + r[4].z;
+        s[3] = r[0].w + r[1].w + r[2].w + r[3].w + r[4].w;
+        s[4] = s[0] - r[0].x + r[5].x;
+        s[5] = s[1] - r[0].y + r[5].y;
+        s[6] = s[2] - r[0].z + r[5].z;
+        s[7] = s[3] - r[0].w + r[5].w;
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+            ring[0][b] = ring[1][b]; ring[1][b] = ring[2][b]; ring[2][b] = ring[3][b]; ring[3][b] = ring[4][b];
+            ring[4][b] = s[b];
+        }
         const int64_t zo = k - 2;   // output plane whose 5-plane window just completed
         if (zo >= 0) {
-            const int64_t x = bx0 + tx, y = by0 + ty;
-            if (x < nx && y < ny) {
-                const uint32_t s = ring[0] + ring[1] + ring[2] + ring[3] + ring[4];
-                dst[(zo * ny + y) * nx + x] = (uint16_t)(s / 2000u);
+#pragma unroll
+            for (int yy = 0; yy < 2; yy++) {
+                const int64_t y = by0 + 2 * ty + yy, x = bx0 + 4 * tx;
+                if (y >= ny) continue;
+                uint16_t v[4];
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    const int e = 4 * yy + b;
+                    v[b] = (uint16_t)((ring[0][e] + ring[1][e] + ring[2][e] + ring[3][e] + ring[4][e]) / 2000u);
+                }
+                uint16_t *row = dst + (zo * ny + y) * nx;
+#pragma unroll
+                for (int b = 0; b < 4; b++)
+                    if (x + b < nx) row[x + b] = v[b];
             }
         }
-        __syncthreads();
     }
 }
 

@@ -1,28 +1,33 @@
-// ec_planar3d.cu -- the planar-form 3D histogram kernel for float32 fields
-// staged by the Tensor Memory Accelerator (the per-voxel changes of
-// ec_slice.h, two stacked quads per thread).
+// ec_planar3d.cu -- the planar-form 3D histogram kernel for fields staged by
+// the Tensor Memory Accelerator (the per-voxel changes of ec_slice.h, two
+// stacked quads per thread): float32 fields with thresholds, and uint16
+// fields with identity levels.
 //
 // One block of 256 threads owns a 64 x 32 column of voxels and walks it
 // along z in work items of `tz` planes.  Per plane:
-//   * the TMA copies a 72 x 34 box of the plane (x from x0-4 so the start is
-//     16-byte aligned, y from y0-1) into a 6-deep shared-memory ring tracked
-//     by mbarriers, four planes ahead of use; out-of-bounds elements arrive as
-//     NaN, which bins to the never-active level, as cells outside the field;
+//   * the TMA copies a box of the plane (float32: 72 x 34 from x0-4; uint16:
+//     80 x 34 from x0-8, so every row starts 16-byte aligned; y from y0-1)
+//     into a 6-deep shared-memory ring tracked by mbarriers, four planes
+//     ahead of use.  Out-of-bounds float elements arrive as NaN, which bins to
+//     the never-active level, as cells outside the field; out-of-bounds
+//     integers arrive as 0, so items whose box reaches outside the field test
+//     coordinates;
 //   * every thread bins fixed pairs of values of two staged planes per
-//     barrier into a 4-deep ring of 16-bit key planes;
+//     barrier into a 4-deep ring of 16-bit key planes (float32: spacing guess
+//     and one threshold read; uint16: one lane-wise minimum with L);
 //   * every thread then handles 8 voxels (x .. x+3 of rows y and y+1): it
 //     keeps rows y-1 .. y+2 of two planes in registers, evaluates the layer
 //     image of plane s and the minimum image of planes s, s+1 (ec_slice.h,
 //     the y pairs between its two rows compared once) and adds each voxel's
 //     changes at its level to the block's shared-memory histograms.
 // Histogram traffic: the shared-memory pipe is the scarce resource (each
-// warp-wide atomic over noisy levels costs about three wavefronts), so the
-// area and volume changes share one 32-bit word per level: the low 17 bits
-// add up 6 - nF (the faces a voxel brings, 0..6) and the high 15 bits count
-// voxels.  Each word is exchanged to zero and decoded into the int32 area and
-// volume rows at every third barrier, so at most 8 planes of 2048 voxels
-// (16384 voxels) reach it between two exchanges: 6 * 16384 < 2^17 and
-// 16384 < 2^15, so neither field overflows.
+// warp-wide atomic over noisy levels costs about three wavefronts), so with
+// the area descriptor the area and volume changes share one 32-bit word per
+// level: the low 17 bits add up 6 - nF (the faces a voxel brings, 0..6) and
+// the high 15 bits count voxels.  Each word is exchanged to zero and decoded
+// into the int32 area and volume rows at every third barrier, so at most 8
+// planes of 2048 voxels (16384 voxels) reach it between two exchanges:
+// 6 * 16384 < 2^17 and 16384 < 2^15, so neither field overflows.
 // Waits on mbarriers are bounded: a wait that gives up sets an error flag,
 // waits (bounded) for the block's copies still in flight and returns.
 #include <cuda.h>
@@ -45,31 +50,51 @@ using fast3d::FBin;
 
 constexpr int kThreads = 256;
 constexpr int TX = 64, TY = 32;              // voxels per plane of a tile
-constexpr int BX = TX + 8, BY = TY + 2;      // staged box: x0-4 .. x0+67, y0-1 .. y0+32
+constexpr int BY = TY + 2;                   // staged rows: y0-1 .. y0+32
 constexpr int KP = 36;                       // key row pitch in words (34 pairs + 2)
 constexpr int KWORDS = BY * KP;              // words per key plane
-constexpr int NS = 6;                        // float plane ring depth
+constexpr int NS = 6;                        // staged plane ring depth
 constexpr int NK = 4;                        // key plane ring depth
-constexpr int FSTRIDE = ((BX * BY * 4 + 127) / 128) * 128 / 4;   // float slot stride (128-byte aligned)
-constexpr int LCAP = 1024;                   // levels the shared histograms hold
-constexpr int HW = LCAP + 1;                 // words per histogram row (level L = never active)
-constexpr int kPairs = BY * (BX - 4) / 2;    // key pairs of one plane: 34 rows x 34
+constexpr int kPairs = BY * 34;              // key pairs of one plane: 34 rows x 34 (x0-2 .. x0+65)
 constexpr int kLeft = kPairs - 32 * 32;      // pairs outside the fixed 4-per-thread shares (132)
 static_assert(kLeft == 132 && 2 * kLeft <= 2 * kThreads, "leftover binning shares");
 
+// Staged box per element type: x from x0 - XOFF (a 16-byte aligned start),
+// BX elements per row (a multiple of 16 bytes); key pair p of a row is at
+// elements XOFF - 2 + 2p.
+template <typename T>
+constexpr int XOFF() { return 16 / (int)sizeof(T); }
+template <typename T>
+constexpr int BXT() { return TX + 2 * XOFF<T>(); }
+template <typename T>
+constexpr int SLOT_BYTES() { return (BXT<T>() * BY * (int)sizeof(T) + 127) / 128 * 128; }
+// Levels the shared histograms hold.
+template <typename T>
+constexpr int LCAP() { return sizeof(T) == 4 ? 1024 : 4096; }
+template <typename T>
+constexpr int HW() { return LCAP<T>() + 1; }   // words per histogram row (level L = never active)
+
 // shared-memory layout (bytes)
-constexpr size_t OFF_KEYS = (size_t)NS * FSTRIDE * 4;
-constexpr size_t OFF_BARS = OFF_KEYS + (size_t)NK * KWORDS * 4;
-constexpr size_t OFF_ABORT = OFF_BARS + NS * 8;
-constexpr size_t OFF_HIST = OFF_ABORT + 16;
-// histogram rows: EC, packed (area, volume), area, volume, perimeter
-enum { H_EC = 0, H_PACK = 1, H_AREA = 2, H_VOL = 3, H_PER = 4 };
+template <typename T>
+constexpr size_t OFF_KEYS() { return (size_t)NS * SLOT_BYTES<T>(); }
+template <typename T>
+constexpr size_t OFF_BARS() { return OFF_KEYS<T>() + (size_t)NK * KWORDS * 4; }
+template <typename T>
+constexpr size_t OFF_HIST() { return OFF_BARS<T>() + NS * 8 + 16; }
+// Histogram rows per descriptor set:
+//   EC (1):                  EC
+//   EC | VOLUME (9):         EC, volume (one +1 atomic per voxel)
+//   EC | AREA | VOLUME (13): EC, packed (free faces, voxels), area, volume
+//   all four (15):           the same and perimeter
 template <int DM>
-constexpr int hist_rows() { return DM == 1 ? 1 : (DM == 13 ? 4 : 5); }
+constexpr int hist_rows() { return DM == 1 ? 1 : (DM == 9 ? 2 : (DM == 13 ? 4 : 5)); }
 template <int DM>
-constexpr size_t off_thr() { return OFF_HIST + (((size_t)hist_rows<DM>() * HW * 4 + 15) & ~(size_t)15); }
-template <int DM>
-constexpr size_t smem_bytes() { return off_thr<DM>() + (size_t)LCAP * 4; }
+constexpr int R_VOL() { return DM == 9 ? 1 : 3; }
+enum { R_EC = 0, R_PACK = 1, R_AREA = 2, R_PER = 4 };
+template <typename T, int DM>
+constexpr size_t off_thr() { return OFF_HIST<T>() + (((size_t)hist_rows<DM>() * HW<T>() * 4 + 15) & ~(size_t)15); }
+template <typename T, int DM>
+constexpr size_t smem_bytes() { return off_thr<T, DM>() + (sizeof(T) == 4 ? (size_t)LCAP<T>() * 4 : 0); }
 
 struct Params {
     int64_t D, H, W;
@@ -77,7 +102,7 @@ struct Params {
     int zc0, zc1;          // planes whose voxels are counted
     int zv0, zv1;          // planes that belong to the field (others read as never active)
     int32_t L;
-    const float *thr;
+    const float *thr;      // float32 fields: thresholds (uint16 fields: identity levels)
     long long *hist;       // int64 [nd][L]
     int rows[kMaxDesc];
     int *err;              // bit 2: a bounded wait gave up
@@ -86,15 +111,17 @@ struct Params {
 };
 
 struct Ctx {
-    float *fring;
+    unsigned char *ring;       // staged planes
     uint32_t *kring;
     uint64_t *bars;
     volatile int *abort_flag;
     int *err;
     FBin fb;
     int tr, tc;
-    uint32_t left0, left1;     // leftover binning pairs: float offset | key offset << 16 | plane << 31, or ~0
+    uint32_t left0, left1;     // leftover binning pairs: row | pair << 16 | plane << 31, or ~0
     int x0, y0, z0, z1, zv0, zv1;
+    int64_t H, W;
+    bool edge;                 // uint16 fields: the item's staged box reaches outside the field
     uint32_t base;             // ring sequence number of plane z0 - 1
     uint32_t parity;
     uint32_t inflight;         // thread 0: ring slots with a TMA copy issued and not yet waited for
@@ -121,32 +148,53 @@ __device__ __forceinline__ uint32_t left_share(int j)
     int row, pair;
     if (j < 64) { row = j >> 1; pair = 32 + (j & 1); }
     else { row = 32 + (j - 64) / 34; pair = (j - 64) % 34; }
-    return (uint32_t)(row * BX + 2 + 2 * pair) | ((uint32_t)(row * KP + pair) << 16) | (plane << 31);
+    return (uint32_t)row | ((uint32_t)pair << 16) | (plane << 31);
 }
 
-template <bool UNI>
-__device__ __forceinline__ void bin_pair2(uint32_t *kp, const float *fp, const FBin &fb)
+// Key pair (row, pair p) of a staged plane.  float32: the spacing guess with
+// one threshold read (UNI) or the general search.  uint16 with identity
+// levels: min(v, L) per lane; on edge items a lane whose cell lies outside
+// the field reads L (out-of-bounds TMA elements are 0).
+template <typename T, bool UNI>
+__device__ __forceinline__ void bin_pair2(const Ctx &c, uint32_t *kp, const T *fp, int row, int pair)
 {
-    const float2 v = *(const float2 *)fp;
-    const uint32_t b0 = UNI ? fast3d::fbin_uniform(v.x, fb) : fast3d::fbin(v.x, fb);
-    const uint32_t b1 = UNI ? fast3d::fbin_uniform(v.y, fb) : fast3d::fbin(v.y, fb);
-    *kp = b0 | (b1 << 16);
+    if constexpr (sizeof(T) == 4) {
+        const float2 v = *(const float2 *)fp;
+        const uint32_t b0 = UNI ? fast3d::fbin_uniform(v.x, c.fb) : fast3d::fbin(v.x, c.fb);
+        const uint32_t b1 = UNI ? fast3d::fbin_uniform(v.y, c.fb) : fast3d::fbin(v.y, c.fb);
+        *kp = b0 | (b1 << 16);
+    } else {
+        const uint32_t L = (uint32_t)c.fb.L;
+        uint32_t k = vmin2(*(const uint32_t *)fp, L | (L << 16));
+        if (c.edge) {
+            const int64_t gy = (int64_t)c.y0 - 1 + row, gx = (int64_t)c.x0 - 2 + 2 * pair;
+            const bool yin = gy >= 0 && gy < c.H;
+            if (!(yin && gx >= 0 && gx < c.W)) k = (k & 0xFFFF0000u) | L;
+            if (!(yin && gx + 1 >= 0 && gx + 1 < c.W)) k = (k & 0x0000FFFFu) | (L << 16);
+        }
+        *kp = k;
+    }
 }
 
 // Bin one staged plane (q = 0: the first of the barrier step, 1: the second):
 // rows tr, tr+16 x pairs tc, tc+16, plus this thread's leftover pairs.
-template <bool UNI>
-__device__ __forceinline__ void bin_plane(const Ctx &c, uint32_t *kp, const float *fp, uint32_t q)
+template <typename T, bool UNI>
+__device__ __forceinline__ void bin_plane(const Ctx &c, uint32_t *kp, const T *fp, uint32_t q)
 {
-    const int fo = c.tr * BX + 2 + 2 * c.tc, ko = c.tr * KP + c.tc;
-    bin_pair2<UNI>(kp + ko, fp + fo, c.fb);
-    bin_pair2<UNI>(kp + ko + 16, fp + fo + 32, c.fb);
-    bin_pair2<UNI>(kp + ko + 16 * KP, fp + fo + 16 * BX, c.fb);
-    bin_pair2<UNI>(kp + ko + 16 * KP + 16, fp + fo + 16 * BX + 32, c.fb);
-    if (c.left0 != ~0u && (c.left0 >> 31) == q)
-        bin_pair2<UNI>(kp + ((c.left0 >> 16) & 0x7FFFu), fp + (c.left0 & 0xFFFFu), c.fb);
-    if (c.left1 != ~0u && (c.left1 >> 31) == q)
-        bin_pair2<UNI>(kp + ((c.left1 >> 16) & 0x7FFFu), fp + (c.left1 & 0xFFFFu), c.fb);
+    constexpr int BX = BXT<T>(), F0 = XOFF<T>() - 2;
+    const int fo = c.tr * BX + F0 + 2 * c.tc, ko = c.tr * KP + c.tc;
+    bin_pair2<T, UNI>(c, kp + ko, fp + fo, c.tr, c.tc);
+    bin_pair2<T, UNI>(c, kp + ko + 16, fp + fo + 32, c.tr, c.tc + 16);
+    bin_pair2<T, UNI>(c, kp + ko + 16 * KP, fp + fo + 16 * BX, c.tr + 16, c.tc);
+    bin_pair2<T, UNI>(c, kp + ko + 16 * KP + 16, fp + fo + 16 * BX + 32, c.tr + 16, c.tc + 16);
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+        const uint32_t lv = e ? c.left1 : c.left0;
+        if (lv != ~0u && (lv >> 31) == q) {
+            const int row = (int)(lv & 0xFFFFu), pair = (int)((lv >> 16) & 0x7FFFu);
+            bin_pair2<T, UNI>(c, kp + row * KP + pair, fp + row * BX + F0 + 2 * pair, row, pair);
+        }
+    }
 }
 
 __device__ __forceinline__ void fill_never(uint32_t *kp, int L)
@@ -158,10 +206,20 @@ __device__ __forceinline__ void fill_never(uint32_t *kp, int L)
     }
 }
 
+template <typename T>
+__device__ __forceinline__ void issue_plane(Ctx &c, const CUtensorMap *tmap, int plane)
+{
+    const uint32_t s = slot_of(c, plane);
+    fast3d::mbar_expect_tx(&c.bars[s], BXT<T>() * BY * (uint32_t)sizeof(T));
+    fast3d::tma_load_plane(c.ring + (size_t)s * SLOT_BYTES<T>(), tmap, c.x0 - XOFF<T>(), c.y0 - 1, plane, &c.bars[s]);
+    c.inflight |= 1u << s;
+}
+
 // Barrier step at h = z0 - 4 + t (t even): thread 0 waits for the staged
 // planes h+3, h+4; the block synchronises; thread 0 requests planes h+NS+1,
 // h+NS+2 into the slots of planes h+1, h+2 (binned at the previous barrier
 // step); the block bins planes h+3, h+4.  Returns false if the block must stop.
+template <typename T>
 __device__ __forceinline__ bool barrier_step(Ctx &c, const CUtensorMap *tmap, int h, int L)
 {
     if (threadIdx.x == 0) {
@@ -193,10 +251,7 @@ __device__ __forceinline__ bool barrier_step(Ctx &c, const CUtensorMap *tmap, in
         for (int q = NS + 1; q <= NS + 2; q++) {
             const int pi = h + q;
             if (pi > c.z1) break;
-            const uint32_t s = slot_of(c, pi);
-            fast3d::mbar_expect_tx(&c.bars[s], BX * BY * 4);
-            fast3d::tma_load_plane(c.fring + s * FSTRIDE, tmap, c.x0 - 4, c.y0 - 1, pi, &c.bars[s]);
-            c.inflight |= 1u << s;
+            issue_plane<T>(c, tmap, pi);
         }
     }
 #pragma unroll
@@ -207,9 +262,9 @@ __device__ __forceinline__ bool barrier_step(Ctx &c, const CUtensorMap *tmap, in
         if (pb < c.zv0 || pb >= c.zv1) {
             fill_never(kp, L);
         } else {
-            const float *fp = c.fring + slot_of(c, pb) * FSTRIDE;
-            if (c.fb.uniform) bin_plane<true>(c, kp, fp, (uint32_t)q);
-            else bin_plane<false>(c, kp, fp, (uint32_t)q);
+            const T *fp = (const T *)(c.ring + (size_t)slot_of(c, pb) * SLOT_BYTES<T>());
+            if (sizeof(T) != 4 || c.fb.uniform) bin_plane<T, true>(c, kp, fp, (uint32_t)q);
+            else bin_plane<T, false>(c, kp, fp, (uint32_t)q);
         }
     }
     return true;
@@ -232,42 +287,47 @@ __device__ __forceinline__ void load_rows(const Ctx &c, int plane, Row5 (&W)[4])
 
 // Add one quad's changes at its levels (key pairs kb = voxels 0, 1 and
 // kd = voxels 2, 3).
-template <int DM>
+template <typename T, int DM>
 __device__ __forceinline__ void add_quad(int *h, uint32_t kb, uint32_t kd, const SliceOut &o)
 {
+    constexpr int hw = HW<T>();
     const uint32_t key[4] = {kb & 0xFFFFu, kb >> 16, kd & 0xFFFFu, kd >> 16};
     const int ecv[4] = {sbyte<0>(o.ec), sbyte<1>(o.ec), sbyte<2>(o.ec), sbyte<3>(o.ec)};
 #pragma unroll
     for (int v = 0; v < 4; v++) {
         int *const e = h + key[v];
-        atomicAdd(e + H_EC * HW, ecv[v]);
+        atomicAdd(e + R_EC * hw, ecv[v]);
         if (DM & 4) {
             // free faces (byte v of o.area, 0..6) plus one voxel at bit 17
             const uint32_t w = __byte_perm(o.area, 0x00020000u, 0x7650u + (uint32_t)v);
-            atomicAdd((unsigned int *)(e + H_PACK * HW), w);
+            atomicAdd((unsigned int *)(e + R_PACK * hw), w);
+        } else if (DM & 8) {
+            atomicAdd(e + R_VOL<DM>() * hw, 1);
         }
         if (DM & 2) {
             const int pv[4] = {sbyte<0>(o.per), sbyte<1>(o.per), sbyte<2>(o.per), sbyte<3>(o.per)};
-            atomicAdd(e + H_PER * HW, pv[v]);
+            atomicAdd(e + R_PER * hw, pv[v]);
         }
     }
 }
 
 // Exchange the packed (free faces, voxels) words of this thread's levels to
 // zero and add them into the area and volume rows.
+template <typename T>
 __device__ __forceinline__ void flush_packed(int *h, int L)
 {
+    constexpr int hw = HW<T>();
     for (int k = threadIdx.x; k <= L; k += kThreads) {
-        const uint32_t w = atomicExch((unsigned int *)(h + H_PACK * HW + k), 0u);
+        const uint32_t w = atomicExch((unsigned int *)(h + R_PACK * hw + k), 0u);
         if (w) {
             const int n = (int)(w >> 17), f = (int)(w & 0x1FFFFu);
-            h[H_AREA * HW + k] += 2 * f - 6 * n;
-            h[H_VOL * HW + k] += n;
+            h[R_AREA * hw + k] += 2 * f - 6 * n;
+            h[3 * hw + k] += n;
         }
     }
 }
 
-template <int DM>
+template <typename T, int DM>
 __device__ __forceinline__ void half_step(Ctx &c, int *hist, Row5 (&P)[4], Row5 (&Q)[4], SliceState &sa,
                                           SliceState &sb, int h)
 {
@@ -278,39 +338,42 @@ __device__ __forceinline__ void half_step(Ctx &c, int *hist, Row5 (&P)[4], Row5 
     } else if (h >= c.z0) {
         SliceOut oa, ob;
         slice_pair<(DM & 4) ? AREA_FREE_FACES : AREA_NONE, PER>(P, Q, sa, sb, oa, ob);
-        add_quad<DM>(hist, P[1].b, P[1].d, oa);
-        add_quad<DM>(hist, P[2].b, P[2].d, ob);
+        add_quad<T, DM>(hist, P[1].b, P[1].d, oa);
+        add_quad<T, DM>(hist, P[2].b, P[2].d, ob);
     }
 }
 
-template <int DM>
+template <typename T, int DM>
 __global__ void __launch_bounds__(kThreads, 2) k_planar3d(const __grid_constant__ CUtensorMap tmap, Params p)
 {
+    constexpr int hw = HW<T>();
     extern __shared__ __align__(128) unsigned char smem[];
     Ctx c;
-    c.fring = (float *)smem;
-    c.kring = (uint32_t *)(smem + OFF_KEYS);
-    c.bars = (uint64_t *)(smem + OFF_BARS);
-    c.abort_flag = (volatile int *)(smem + OFF_ABORT);
+    c.ring = smem;
+    c.kring = (uint32_t *)(smem + OFF_KEYS<T>());
+    c.bars = (uint64_t *)(smem + OFF_BARS<T>());
+    c.abort_flag = (volatile int *)(smem + OFF_BARS<T>() + NS * 8);
     c.err = p.err;
-    int *const hist = (int *)(smem + OFF_HIST);
-    float *const thr = (float *)(smem + off_thr<DM>());
+    int *const hist = (int *)(smem + OFF_HIST<T>());
     const int L = p.L;
-    for (int i = threadIdx.x; i < hist_rows<DM>() * HW; i += kThreads) hist[i] = 0;
-    for (int k = threadIdx.x; k < L; k += kThreads) thr[k] = p.thr[k];
+    for (int i = threadIdx.x; i < hist_rows<DM>() * hw; i += kThreads) hist[i] = 0;
     c.fb = FBin{};
-    c.fb.t = thr;
     c.fb.L = L;
-    c.fb.t0 = p.thr[0];
-    c.fb.tl = p.thr[L - 1];
-    c.fb.inv = (L > 1 && c.fb.tl > c.fb.t0) ? (float)(L - 1) / (c.fb.tl - c.fb.t0) : 0.f;
-    c.fb.lm1 = (float)(L - 1);
-    c.fb.off = 0.f;
-    c.fb.uniform = 0;
-    if (p.uni[0]) {
-        c.fb.uniform = 1;
-        c.fb.inv = __int_as_float(p.uni[1]);
-        c.fb.off = __int_as_float(p.uni[2]);
+    if constexpr (sizeof(T) == 4) {
+        float *const thr = (float *)(smem + off_thr<T, DM>());
+        for (int k = threadIdx.x; k < L; k += kThreads) thr[k] = p.thr[k];
+        c.fb.t = thr;
+        c.fb.t0 = p.thr[0];
+        c.fb.tl = p.thr[L - 1];
+        c.fb.inv = (L > 1 && c.fb.tl > c.fb.t0) ? (float)(L - 1) / (c.fb.tl - c.fb.t0) : 0.f;
+        c.fb.lm1 = (float)(L - 1);
+        c.fb.off = 0.f;
+        c.fb.uniform = 0;
+        if (p.uni[0]) {
+            c.fb.uniform = 1;
+            c.fb.inv = __int_as_float(p.uni[1]);
+            c.fb.off = __int_as_float(p.uni[2]);
+        }
     }
     if (threadIdx.x == 0) {
         for (int i = 0; i < NS; i++) fast3d::mbar_init(&c.bars[i], 1);
@@ -328,6 +391,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_planar3d(const __grid_constant_
     c.give_up = p.test_give_up;
     c.zv0 = p.zv0;
     c.zv1 = p.zv1;
+    c.H = p.H;
+    c.W = p.W;
     uint32_t seq = 0;
     uint32_t nbar = 0;   // barrier steps since the packed words were last exchanged
     const int nitems = p.nbx * p.nby * p.nbz;
@@ -340,51 +405,52 @@ __global__ void __launch_bounds__(kThreads, 2) k_planar3d(const __grid_constant_
         c.y0 = by * TY;
         c.z0 = p.zc0 + bz * p.tz;
         c.z1 = min(c.z0 + p.tz, p.zc1);
+        // binned cells x0-2 .. x0+65, y0-1 .. y0+32
+        c.edge = c.x0 < 2 || c.x0 + 66 > p.W || c.y0 < 1 || c.y0 + 33 > p.H;
         __syncthreads();   // the previous item is done with both rings
         c.base = seq;
         if (threadIdx.x == 0) {
             for (int q = 0; q < NS - 2; q++) {
                 const int pz = c.z0 - 1 + q;
                 if (pz > c.z1) break;
-                const uint32_t s = slot_of(c, pz);
-                fast3d::mbar_expect_tx(&c.bars[s], BX * BY * 4);
-                fast3d::tma_load_plane(c.fring + s * FSTRIDE, &tmap, c.x0 - 4, c.y0 - 1, pz, &c.bars[s]);
-                c.inflight |= 1u << s;
+                issue_plane<T>(c, &tmap, pz);
             }
         }
         const int nsteps = c.z1 - c.z0 + 4;
         for (int t = 0; t < nsteps; t += 2) {
             const int h = c.z0 - 4 + t;
-            if (!barrier_step(c, &tmap, h, L)) return;
+            if (!barrier_step<T>(c, &tmap, h, L)) return;
             if (DM & 4) {
                 if (++nbar == 3) {
                     nbar = 0;
-                    flush_packed(hist, L);
+                    flush_packed<T>(hist, L);
                 }
             }
-            half_step<DM>(c, hist, W0, W1, sa, sb, h);
-            if (t + 1 < nsteps) half_step<DM>(c, hist, W1, W0, sa, sb, h + 1);
+            half_step<T, DM>(c, hist, W0, W1, sa, sb, h);
+            if (t + 1 < nsteps) half_step<T, DM>(c, hist, W1, W0, sa, sb, h + 1);
         }
         seq += (uint32_t)(c.z1 - c.z0 + 2);
     }
     __syncthreads();
     if (DM & 4) {
-        flush_packed(hist, L);
+        flush_packed<T>(hist, L);
         __syncthreads();
     }
     // global rows are [nd][L] in the order EC, PER, AREA, VOL; level L is dropped
     for (int k = threadIdx.x; k < L; k += kThreads) {
         long long *g = p.hist;
-        int v = hist[H_EC * HW + k];
+        int v = hist[R_EC * hw + k];
         if (v) atomicAdd((unsigned long long *)&g[(size_t)p.rows[0] * L + k], (unsigned long long)(long long)v);
         if (DM & 2) {
-            v = hist[H_PER * HW + k];
+            v = hist[R_PER * hw + k];
             if (v) atomicAdd((unsigned long long *)&g[(size_t)p.rows[1] * L + k], (unsigned long long)(long long)v);
         }
         if (DM & 4) {
-            v = hist[H_AREA * HW + k];
+            v = hist[R_AREA * hw + k];
             if (v) atomicAdd((unsigned long long *)&g[(size_t)p.rows[2] * L + k], (unsigned long long)(long long)v);
-            v = hist[H_VOL * HW + k];
+        }
+        if (DM & 8) {
+            v = hist[R_VOL<DM>() * hw + k];
             if (v) atomicAdd((unsigned long long *)&g[(size_t)p.rows[3] * L + k], (unsigned long long)(long long)v);
         }
     }
@@ -408,11 +474,11 @@ static int plan_tile_z(int64_t columns, int planes, int grid)
     return best;
 }
 
-template <int DM>
+template <typename T, int DM>
 static int launch_dm(const CUtensorMap &map, Params p, int tile_z, int num_sms, int grid_override, cudaStream_t s)
 {
-    auto kern = k_planar3d<DM>;
-    const size_t smem = smem_bytes<DM>();
+    auto kern = k_planar3d<T, DM>;
+    const size_t smem = smem_bytes<T, DM>();
     EC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
@@ -432,9 +498,10 @@ static int launch_dm(const CUtensorMap &map, Params p, int tile_z, int num_sms, 
 
 }  // namespace planar3d
 
-// The planar kernel for float32 fields the TMA can stage (start 16-byte
-// aligned, rows a multiple of 4 floats) with at most 1024 levels and the
-// descriptor sets EC, EC|AREA|VOLUME or all four.  Returns
+// The planar kernel for fields the TMA can stage (start 16-byte aligned, rows
+// a multiple of 16 bytes): float32 with thresholds, at most 1024 levels and
+// the descriptor sets EC, EC|AREA|VOLUME or all four; uint16 with identity
+// levels, at most 4096 levels and EC or EC|VOLUME.  Returns
 // EC_ERR_UNSUPPORTED (without launching) for anything else.
 int launch_planar_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha, int tile_z,
                      int grid_override, int num_sms, int *err_flag, cudaStream_t s, const int zrange[4])
@@ -443,10 +510,14 @@ int launch_planar_3d(const void *field, const int64_t dims[3], const BinArgs &ba
     uint32_t desc = 0;
     for (int i = 0; i < kMaxDesc; i++)
         if (ha.rows.row[i] >= 0) desc |= 1u << i;
-    if (ba.dtype != EC_F32 || ba.L < 1 || ba.L > LCAP || !ba.thr || (desc != 1u && desc != 13u && desc != 15u))
-        return EC_ERR_UNSUPPORTED;
-    if ((dims[2] % 4) != 0 || ((uintptr_t)field % 16) != 0 || dims[0] > INT32_MAX / 2 || dims[1] > INT32_MAX / 2 ||
-        dims[2] > INT32_MAX / 2)
+    const bool f32 = ba.dtype == EC_F32 && ba.thr && ba.L >= 1 && ba.L <= LCAP<float>() &&
+                     (desc == 1u || desc == 13u || desc == 15u);
+    const bool u16 = ba.dtype == EC_U16 && !ba.thr && ba.L >= 1 && ba.L <= LCAP<uint16_t>() &&
+                     (desc == 1u || desc == 9u);
+    if (!f32 && !u16) return EC_ERR_UNSUPPORTED;
+    const int esz = f32 ? 4 : 2;
+    if ((dims[2] * esz) % 16 != 0 || ((uintptr_t)field % 16) != 0 || dims[0] > INT32_MAX / 2 ||
+        dims[1] > INT32_MAX / 2 || dims[2] > INT32_MAX / 2)
         return EC_ERR_UNSUPPORTED;
     PFN_cuTensorMapEncodeTiled_v12000 enc = (PFN_cuTensorMapEncodeTiled_v12000)tma_encode_fn();
     if (!enc) return EC_ERR_UNSUPPORTED;
@@ -460,7 +531,7 @@ int launch_planar_3d(const void *field, const int64_t dims[3], const BinArgs &ba
     p.nby = (int)((p.H + TY - 1) / TY);
     if (p.zc1 <= p.zc0) return EC_OK;
     p.L = ba.L;
-    p.thr = (const float *)ba.thr;
+    p.thr = f32 ? (const float *)ba.thr : nullptr;
     p.hist = ha.hist;
     for (int i = 0; i < kMaxDesc; i++) p.rows[i] = ha.rows.row[i];
     p.err = err_flag;
@@ -469,20 +540,27 @@ int launch_planar_3d(const void *field, const int64_t dims[3], const BinArgs &ba
     CUtensorMap map;
     memset(&map, 0, sizeof map);
     cuuint64_t gdim[3] = {(cuuint64_t)p.W, (cuuint64_t)p.H, (cuuint64_t)p.D};
-    cuuint64_t gstride[2] = {(cuuint64_t)p.W * 4, (cuuint64_t)p.W * p.H * 4};
-    cuuint32_t box[3] = {(cuuint32_t)BX, (cuuint32_t)BY, 1};
+    cuuint64_t gstride[2] = {(cuuint64_t)(p.W * esz), (cuuint64_t)(p.W * p.H * esz)};
+    cuuint32_t box[3] = {(cuuint32_t)(f32 ? BXT<float>() : BXT<uint16_t>()), (cuuint32_t)BY, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(field), gdim, gstride, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA);
+    // float32: out-of-bounds elements read NaN (never active); uint16: zero,
+    // replaced by L through the edge items' coordinate test
+    CUresult r = enc(&map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 3,
+                     const_cast<void *>(field), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     f32 ? CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA : CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return EC_ERR_UNSUPPORTED;
-    if (!ba.uni_ready) {
-        const int rc = launch_uniform_check((const float *)ba.thr, ba.L, err_flag + 2, s);
-        if (rc) return rc;
+    if (f32) {
+        if (!ba.uni_ready) {
+            const int rc = launch_uniform_check((const float *)ba.thr, ba.L, err_flag + 2, s);
+            if (rc) return rc;
+        }
+        if (desc == 1u) return launch_dm<float, 1>(map, p, tile_z, num_sms, grid_override, s);
+        if (desc == 13u) return launch_dm<float, 13>(map, p, tile_z, num_sms, grid_override, s);
+        return launch_dm<float, 15>(map, p, tile_z, num_sms, grid_override, s);
     }
-    if (desc == 1u) return launch_dm<1>(map, p, tile_z, num_sms, grid_override, s);
-    if (desc == 13u) return launch_dm<13>(map, p, tile_z, num_sms, grid_override, s);
-    return launch_dm<15>(map, p, tile_z, num_sms, grid_override, s);
+    if (desc == 1u) return launch_dm<uint16_t, 1>(map, p, tile_z, num_sms, grid_override, s);
+    return launch_dm<uint16_t, 9>(map, p, tile_z, num_sms, grid_override, s);
 }
 
 }  // namespace ec

@@ -25,6 +25,9 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -217,6 +220,63 @@ extern "C" int ec_curve_3d_stream(ec_ctx *ctx, const void *host_field, ec_slab_f
 
 namespace {
 
+// Reader threads that live for one call: each slab's byte range is split
+// into nthr contiguous parts read in parallel (page-cache copies are bound
+// by per-core memory bandwidth, so more readers read faster).
+struct ReaderPool {
+    std::vector<std::thread> th;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::function<void(int)> job;
+    uint64_t gen = 0;
+    int pending = 0;
+    bool stop = false;
+    explicit ReaderPool(int n)
+    {
+        for (int t = 1; t < n; t++)
+            th.emplace_back([this, t]() {
+                uint64_t seen = 0;
+                for (;;) {
+                    std::function<void(int)> fn;
+                    {
+                        std::unique_lock<std::mutex> lk(mu);
+                        cv.wait(lk, [&] { return stop || gen != seen; });
+                        if (stop) return;
+                        seen = gen;
+                        fn = job;
+                    }
+                    fn(t);
+                    std::lock_guard<std::mutex> lk(mu);
+                    if (--pending == 0) done_cv.notify_one();
+                }
+            });
+    }
+    int size() const { return (int)th.size() + 1; }
+    // run fn(0 .. size()-1), part 0 on the calling thread
+    void run(const std::function<void(int)> &fn)
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            job = fn;
+            pending = (int)th.size();
+            gen++;
+        }
+        cv.notify_all();
+        fn(0);
+        std::unique_lock<std::mutex> lk(mu);
+        done_cv.wait(lk, [&] { return pending == 0; });
+    }
+    ~ReaderPool()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stop = true;
+        }
+        cv.notify_all();
+        for (auto &x : th) x.join();
+    }
+};
+
 struct FileSlabs {
     int fd = -1;
     int64_t offset = 0, d = 0;
@@ -226,8 +286,10 @@ struct FileSlabs {
     int next = 0;
     int64_t bad_plane = -1;             // first plane whose read failed
     int bad_errno = 0;
+    ReaderPool *pool = nullptr;
     ~FileSlabs()
     {
+        delete pool;
         for (int i = 0; i < 2; i++) {
             if (copied[i]) { cudaEventSynchronize(copied[i]); cudaEventDestroy(copied[i]); }
             if (pinned[i]) cudaFreeHost(pinned[i]);
@@ -246,22 +308,23 @@ int file_producer(void *user, int64_t z0, int64_t z1, void *dst_dev, void *strea
     const int i = f.next;
     f.next ^= 1;
     if (cudaEventSynchronize(f.copied[i]) != cudaSuccess) return 2;
-    // large slabs are read by several threads in plane-aligned chunks
-    const int64_t nplanes = b - a;
-    const int nthr = (int)std::max<int64_t>(1, std::min<int64_t>({8, nplanes, (int64_t)(bytes >> 22)}));
+    // the slab's bytes in equal contiguous parts, one per reader (parts of at
+    // least 1 MiB)
+    const int nthr = (int)std::max<size_t>(1, std::min<size_t>((size_t)f.pool->size(), bytes >> 20));
+    const int64_t base_off = f.offset + a * (int64_t)f.plane;
     std::vector<int64_t> bad(nthr, -1);
     std::vector<int> bad_err(nthr, 0);
     auto read_part = [&](int t) {
-        const int64_t p0 = nplanes * t / nthr, p1 = nplanes * (t + 1) / nthr;
-        char *p = (char *)f.pinned[i] + (size_t)p0 * f.plane;
-        off_t off = (off_t)(f.offset + (a + p0) * (int64_t)f.plane);
-        size_t left = (size_t)(p1 - p0) * f.plane;
-        const size_t total = left;
+        if (t >= nthr) return;
+        const size_t b0 = bytes * (size_t)t / (size_t)nthr, b1 = bytes * (size_t)(t + 1) / (size_t)nthr;
+        char *p = (char *)f.pinned[i] + b0;
+        off_t off = (off_t)(base_off + (int64_t)b0);
+        size_t left = b1 - b0;
         while (left > 0) {
             const ssize_t r = pread(f.fd, p, left, off);
             if (r < 0 && errno == EINTR) continue;
             if (r <= 0) {
-                bad[t] = a + p0 + (int64_t)((total - left) / f.plane);
+                bad[t] = a + (int64_t)((b1 - left) / f.plane);
                 bad_err[t] = r < 0 ? errno : 0;
                 return;
             }
@@ -270,14 +333,8 @@ int file_producer(void *user, int64_t z0, int64_t z1, void *dst_dev, void *strea
             left -= (size_t)r;
         }
     };
-    if (nthr == 1) {
-        read_part(0);
-    } else {
-        std::vector<std::thread> th;
-        for (int t = 1; t < nthr; t++) th.emplace_back(read_part, t);
-        read_part(0);
-        for (auto &x : th) x.join();
-    }
+    if (nthr == 1) read_part(0);
+    else f.pool->run(read_part);
     for (int t = 0; t < nthr; t++)
         if (bad[t] >= 0) {
             f.bad_plane = bad[t];
@@ -334,6 +391,7 @@ extern "C" int ec_curve_3d_file(ec_ctx *ctx, const char *path, int64_t offset, c
             EC_CUDA(cudaEventCreateWithFlags(&f.copied[i], cudaEventDisableTiming));
         }
     }
+    f.pool = new ReaderPool((int)std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
     rc = ec_curve_3d_stream(ctx, nullptr, file_producer, &f, dims, dtype, thresholds_host, L, connectivity,
                             descriptors, slab_planes, device_mem_cap, out_host);
     if (rc && f.bad_plane >= 0) {

@@ -70,6 +70,9 @@ def lib():
             L.ec_vertex_table_2d.argtypes = [P]
             L.ec_vertex_table_3d.argtypes = [P]
             L.ec_vertex_table_3d_ec6.argtypes = [P]
+            L.ec_bmp_read.argtypes = [ctypes.c_char_p, P, P]
+            L.ec_curve_2d_bmp.argtypes = [P, ctypes.c_char_p, P, I32, ctypes.c_int, ctypes.c_uint32, P]
+            L.ec_curve_3d_bmp.argtypes = [P, P, I64, P, I32, ctypes.c_int, ctypes.c_uint32, I64, ctypes.c_size_t, P]
             L.ec_selfcheck_rules.restype = I64
             L.ec_server_create.argtypes = [P, ctypes.c_size_t, I32, ctypes.POINTER(P)]
             L.ec_server_submit.argtypes = [P, ctypes.POINTER(FieldDesc), ctypes.POINTER(ctypes.c_uint64)]
@@ -423,6 +426,48 @@ def curve_3d_file(path, dims, dtype, thresholds=None, L=None, offset=0, connecti
                                   None if thr is None else thr.ctypes.data_as(ctypes.c_void_p), int(L),
                                   int(connectivity), int(descriptors), int(slab_planes),
                                   ctypes.c_size_t(int(device_mem_cap)), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def bmp_read(path) -> np.ndarray:
+    """The pixels of a grayscale BMP as uint8 [h, w], row 0 = the top row (ec_bmp_read)."""
+    dims = (ctypes.c_int64 * 2)()
+    _check(lib().ec_bmp_read(os.fsencode(path), dims, None))
+    out = np.zeros((dims[0], dims[1]), dtype=np.uint8)
+    _check(lib().ec_bmp_read(os.fsencode(path), dims, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def curve_2d_bmp(path, thresholds=None, L=None, connectivity=8, descriptors=EC_DESC_EC,
+                 ctx: Context | None = None, device: int = 0):
+    """Curves of one grayscale BMP image (ec_curve_2d_bmp): int64 numpy [rows, L]."""
+    ctx = ctx or default_context(device)
+    thr = None if thresholds is None else np.ascontiguousarray(np.asarray(thresholds, dtype=np.uint8))
+    L = (thr.size if thr is not None else None) if L is None else L
+    if L is None:
+        raise ValueError("L is required with identity levels")
+    out = np.zeros((n_rows(descriptors), L), dtype=np.int64)
+    _check(lib().ec_curve_2d_bmp(ctx.handle, os.fsencode(path),
+                                 None if thr is None else thr.ctypes.data_as(ctypes.c_void_p), int(L),
+                                 int(connectivity), int(descriptors), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def curve_3d_bmp(paths, thresholds=None, L=None, connectivity=26, descriptors=EC_DESC_EC, slab_planes=64,
+                 device_mem_cap=0, ctx: Context | None = None, device: int = 0):
+    """Curves of a stack of BMP slices, paths[z] = plane z (ec_curve_3d_bmp): int64 numpy [rows, L]."""
+    ctx = ctx or default_context(device)
+    thr = None if thresholds is None else np.ascontiguousarray(np.asarray(thresholds, dtype=np.uint8))
+    L = (thr.size if thr is not None else None) if L is None else L
+    if L is None:
+        raise ValueError("L is required with identity levels")
+    enc = [os.fsencode(p) for p in paths]
+    arr = (ctypes.c_char_p * len(enc))(*enc)
+    out = np.zeros((n_rows(descriptors), L), dtype=np.int64)
+    _check(lib().ec_curve_3d_bmp(ctx.handle, ctypes.cast(arr, ctypes.c_void_p), len(enc),
+                                 None if thr is None else thr.ctypes.data_as(ctypes.c_void_p), int(L),
+                                 int(connectivity), int(descriptors), int(slab_planes),
+                                 ctypes.c_size_t(int(device_mem_cap)), out.ctypes.data_as(ctypes.c_void_p)))
     return out
 
 

@@ -111,6 +111,27 @@ def test_planar_tma_shapes(ctx, shape, uniform):
         check(ctx, f, thr, L, desc=desc, algos=[ec.ALGO_PLANAR])
 
 
+# uint16 fields with identity levels (rows a multiple of 8 values) take the
+# same kernel with an 80 x 34 TMA box; out-of-field cells read 0 there, so
+# tiles at the field's edge are the ones to test.
+SHAPES3_TMA16 = [(1, 1, 8), (3, 5, 16), (2, 33, 72), (17, 31, 136), (70, 65, 64), (9, 64, 8), (33, 97, 104)]
+
+
+@pytest.mark.parametrize("shape", SHAPES3_TMA16)
+def test_planar_tma_uint16_identity_levels(ctx, shape):
+    rng = np.random.default_rng(zlib.crc32(repr((shape, "tma16")).encode()))
+    for L in (1, 37, 4096):
+        f = rng.integers(0, L + 40, size=shape).astype(np.uint16)   # values at and above L too
+        for desc in (1, 9):
+            check(ctx, f, None, L, desc=desc, algos=[ec.ALGO_PLANAR])
+    g = np.clip(workloads.grf_nd(int(rng.integers(1 << 30)), shape, 2.0).numpy() * 600 + 2000, 0, 4095)
+    g = g.astype(np.uint16)
+    check(ctx, g, None, 4096, desc=9, algos=[ec.ALGO_PLANAR, ec.ALGO_VOXEL])
+    for slab in (1, 5, 64):
+        got = ec.curve_3d_stream(g, L=4096, descriptors=9, slab_planes=slab, ctx=ctx)
+        np.testing.assert_array_equal(got, oracle.ec_curves(g, None, 4096, 26, 9))
+
+
 def test_planar_tma_item_depths_and_constant_field(ctx):
     """Work items of 1..7 and 64 planes; a constant field puts every voxel of a
     block on one level, the largest count the packed area/volume words take

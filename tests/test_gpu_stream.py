@@ -49,10 +49,14 @@ def test_stream_odd_shapes_and_dtypes(ctx):
 
 
 def test_hashbox_generator_matches_oracle_definition(ctx):
-    dev = ec.gen_hashbox_u16(4, -3, 1000, 2045, 37, 19, 6)
-    torch.cuda.synchronize()
-    np.testing.assert_array_equal(dev.cpu().numpy().astype(np.int32),
-                                  oracle.hashbox_u16(4, -3, 1000, 2045, 37, 19, 6).astype(np.int32))
+    # partial and whole 64 x 32 output tiles, one and several planes, origins
+    # on both sides of the 16-bit coordinate wrap
+    for origin, n in (((-3, 1000, 2045), (37, 19, 6)), ((0, 0, 0), (64, 32, 1)), ((65530, 7, -2), (130, 70, 3)),
+                      ((5, 5, 5), (1, 1, 1)), ((100, 200, 300), (200, 33, 9))):
+        dev = ec.gen_hashbox_u16(4, *origin, *n)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(dev.cpu().numpy().astype(np.int32),
+                                      oracle.hashbox_u16(4, *origin, *n).astype(np.int32), err_msg=repr((origin, n)))
 
 
 @pytest.mark.parametrize("origin,n", [((0, 0, 0), 512), ((700, 900, 1100), 96)])
