@@ -197,64 +197,141 @@ def time_device(fn, steps):
     return st.elapsed_time(en) / steps
 
 
-def batched_vs_per_field(ec, ctx, n_requests, seed=5):
-    """The served workload's mix (70 % 2D uint8, 30 % 3D float32, uneven
-    sizes and level counts): one launch per field, one batched persistent
-    launch, and the continuous-admission server fed with Poisson arrivals."""
+def stratified_subset(reqs, per_stratum, seed):
+    """Indices of a stratified sample of the request stream: for each kind
+    (2D, 3D) the requests split into side quartiles and per_stratum drawn
+    from each, plus the largest field of each kind."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    pick = set()
+    for nd in (2, 3):
+        idx = [i for i, r in enumerate(reqs) if r["ndim"] == nd]
+        idx.sort(key=lambda i: reqs[i]["side"])
+        pick.add(idx[-1])
+        for q in range(4):
+            part = idx[len(idx) * q // 4:len(idx) * (q + 1) // 4]
+            pick.update(int(i) for i in rng.choice(part, size=min(per_stratum, len(part)), replace=False))
+    return sorted(pick)
+
+
+def config5_section(ec, ctx, n_requests, seed=5, loads=(0.5, 0.9, 1.2), with_oracle=True):
+    """The batched/served workload at its stated size: n_requests requests,
+    70 % 2D uint8 (side log-uniform 64..4096, 256 levels, EC+perimeter+area)
+    and 30 % 3D float32 (side log-uniform 32..512, 64..1024 uniform
+    thresholds, EC+perimeter+area+volume), each a smoothed GRF generated on
+    the device.  Timed three ways on the same device-resident fields: one
+    ec_curve call per field; one ec_batch (persistent launch in a CUDA
+    graph) with the autotuner choosing its plan (tuned on the first, untimed
+    call) and with the default plan; and the continuous-admission server
+    (slots tuned the same way, an untimed burst first) under Poisson
+    arrivals at 0.5, 0.9 and 1.2 of its closed-loop capacity.  All paths
+    must agree; a stratified subset of at least 256 requests (with the
+    largest field of each kind) is checked against the oracle."""
     import numpy as np
     import torch
     from paper_2311_11740_gb300 import workloads
-    reqs = workloads.request_stream(seed=seed, n=n_requests, max_2d=2048, max_3d=256)
+    reqs = workloads.request_stream(seed=seed, n=n_requests, max_2d=4096, max_3d=512)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     fields, cells = [], 0
     for r in reqs:
-        f, thr = workloads.request_field(r, device="cuda")
+        f, thr = workloads.request_field_device(r, device="cuda")
         fields.append(dict(field=f, thresholds=thr, L=r["L"], descriptors=7 if r["ndim"] == 2 else 15))
         cells += f.numel()
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    field_bytes = sum(d["field"].numel() * d["field"].element_size() for d in fields)
+
+    # one launch sequence per field
     outs = [ec.curve(d["field"], d["thresholds"], L=d["L"], descriptors=d["descriptors"], ctx=ctx) for d in fields]
-    ec.batch(fields, ctx=ctx)
     per_ms = time_device(lambda: [ec.curve(d["field"], d["thresholds"], L=d["L"], descriptors=d["descriptors"],
-                                           ctx=ctx, out=o) for d, o in zip(fields, outs)], 3)
-    bat_ms = time_device(lambda: ec.batch(fields, ctx=ctx), 5)
-    same = all(torch.equal(a, b) for a, b in zip(outs, ec.batch(fields, ctx=ctx)))
-    # served: page-locked host fields, one long-lived server warmed by one
-    # untimed burst; a closed-loop pass (the whole burst submitted at once)
-    # gives the server's capacity, then Poisson arrivals at 0.9 of that
-    # capacity give the latency distribution
-    host = [(d["field"].cpu().pin_memory(), None if d["thresholds"] is None else d["thresholds"].cpu().numpy(),
-             d["L"], d["descriptors"]) for d in fields]
-    want = [o.cpu().numpy() for o in outs]
-    sv = ec.Server(device_mem_budget=8 << 30, max_slots=8, ctx=ctx)
-    served_ok = all(np.array_equal(sv.wait(t, 600000), w) for t, w in zip(sv.submit_many(host), want))
+                                           ctx=ctx, out=o) for d, o in zip(fields, outs)], 2)
+    # one batched launch: default plan, then the autotuned plan
+    plain = ec.Batch(fields, ctx=ctx)
+    plain.run()
+    plain_ms = time_device(plain.run, 3)
+    same = all(torch.equal(a, b) for a, b in zip(outs, plain.outs))
+    tctx = ec.Context(torch.cuda.current_device())
+    tctx.set_option(ec.EC_OPT_AUTOTUNE, 1)
+    tuned = ec.Batch(fields, ctx=tctx)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tickets = sv.submit_many(host)   # the whole burst in one call
+    tuned.run()   # the first batch of its mix class times the candidate plans
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    tuned_ms = time_device(tuned.run, 3)
+    same &= all(torch.equal(a, b) for a, b in zip(outs, tuned.outs))
+    plan = tuned.tuned_plan()
+
+    # served: device-resident fields, host thresholds and outputs
+    host_thr = [None if d["thresholds"] is None else d["thresholds"].cpu().numpy() for d in fields]
+    reqs_sv = [dict(field=d["field"], thresholds=t, L=d["L"], descriptors=d["descriptors"])
+               for d, t in zip(fields, host_thr)]
+    want = [o.cpu().numpy() for o in outs]
+    sv = ec.Server(device_mem_budget=8 << 30, max_slots=8, ctx=tctx)
+    served_ok = all(np.array_equal(sv.wait(t, 600000), w) for t, w in zip(sv.submit_many(reqs_sv), want))
+    t0 = time.perf_counter()
+    tickets = sv.submit_many(reqs_sv)   # closed loop: the whole stream at once
     sv.wait_all(600000)
     cap_s = time.perf_counter() - t0
     served_ok &= all(np.array_equal(sv.result(t), w) for t, w in zip(tickets, want))
-    rate = 0.9 * len(host) / cap_s
+    served = {"closed_loop_gcells_s": cells / cap_s / 1e9, "closed_loop_ms": cap_s * 1e3, "slots": 8,
+              "fields": "device-resident (read in place); thresholds and outputs through host memory",
+              "loads": []}
     rng = np.random.default_rng(seed)
-    gaps = rng.exponential(1.0 / rate, size=len(host))
-    sv.reset_stats()
-    t0 = time.perf_counter()
-    due = t0
-    tickets = []
-    for (f, thr, Lr, dsc), g in zip(host, gaps):
-        due += g
-        while time.perf_counter() < due:
-            pass
-        tickets.append(sv.submit(f, thr, L=Lr, descriptors=dsc))
-    served_ok &= all(np.array_equal(sv.wait(t, 600000), w) for t, w in zip(tickets, want))
-    span = time.perf_counter() - t0
-    stats = sv.stats()
+    for rho in loads:
+        rate = rho * len(reqs_sv) / cap_s
+        gaps = rng.exponential(1.0 / rate, size=len(reqs_sv))
+        sv.reset_stats()
+        t0 = time.perf_counter()
+        due = t0
+        tickets = []
+        for r, g in zip(reqs_sv, gaps):
+            due += g
+            while time.perf_counter() < due:
+                pass
+            tickets.append(sv.submit(**r))
+        served_ok &= all(np.array_equal(sv.wait(t, 600000), w) for t, w in zip(tickets, want))
+        span = time.perf_counter() - t0
+        st = sv.stats()
+        served["loads"].append({"offered_load": rho, "offered_rate_req_s": rate, "gcells_s": cells / span / 1e9,
+                                "p50_us": st["p50_us"], "p99_us": st["p99_us"], "mean_us": st["mean_us"]})
     sv.close()
-    return {"workload": f"{len(fields)} requests, seed {seed}: 70% 2D uint8 (side log-uniform 64..2048, 256 levels), "
-                        f"30% 3D float32 (side log-uniform 32..256, 64..1024 levels), smoothed GRFs",
-            "cells": cells, "per_field_gcells_s": cells / per_ms / 1e6, "batched_gcells_s": cells / bat_ms / 1e6,
-            "per_field_ms": per_ms, "batched_ms": bat_ms, "identical": bool(same and served_ok),
-            "served": {"closed_loop_gcells_s_incl_h2d": cells / cap_s / 1e9,
-                       "offered_rate_req_s": rate, "offered_load": 0.9,
-                       "gcells_s_incl_h2d": cells / span / 1e9,
-                       "p50_us": stats["p50_us"], "p99_us": stats["p99_us"], "slots": 8,
-                       "host_fields": "page-locked"}}
+    res = {"workload": f"{len(fields)} requests, seed {seed}: 70% 2D uint8 (side log-uniform 64..4096, 256 "
+                       f"levels, EC+perimeter+area), 30% 3D float32 (side log-uniform 32..512, 64..1024 "
+                       f"thresholds, all four descriptors), smoothed GRFs (sigma 2..10) generated on the device",
+           "requests": len(fields), "cells": cells, "field_bytes": field_bytes, "generate_s": gen_s,
+           "largest": {"2d_side": max(r["side"] for r in reqs if r["ndim"] == 2),
+                       "3d_side": max(r["side"] for r in reqs if r["ndim"] == 3)},
+           "per_field_ms": per_ms, "per_field_gcells_s": cells / per_ms / 1e6,
+           "batched_default_ms": plain_ms, "batched_default_gcells_s": cells / plain_ms / 1e6,
+           "batched_ms": tuned_ms, "batched_gcells_s": cells / tuned_ms / 1e6,
+           "autotune": {"on": True, "tuning_call_s": tune_s,
+                        "plan": None if plan is None else dict(zip(("tz3", "grid", "rows2d"), plan)),
+                        "candidates": "3D item depth 16/32/64, 2D item rows 32/64/128, grid all-resident or "
+                                      "one block per SM (coordinate descent)"},
+           "served": served, "identical": bool(same and served_ok)}
+    del tuned, plain
+    tctx.close()
+    if with_oracle:
+        import oracle
+        sub = stratified_subset(reqs, 32, seed)
+        t0 = time.perf_counter()
+        ok = True
+        for i in sub:
+            d = fields[i]
+            f = d["field"].cpu().numpy()
+            thr = None if d["thresholds"] is None else d["thresholds"].cpu().numpy()
+            conn = 8 if f.ndim == 2 else 26
+            ok &= bool(np.array_equal(oracle.ec_curves(f, thr, d["L"], conn, d["descriptors"]), want[i]))
+        res["identical_to_oracle"] = ok
+        res["oracle_subset"] = {"requests": len(sub), "cells": int(sum(fields[i]["field"].numel() for i in sub)),
+                                "strata": "2D and 3D each split into side quartiles, 32 drawn per quartile, "
+                                          "plus the largest field of each kind",
+                                "oracle_s": time.perf_counter() - t0}
+    del fields, outs
+    torch.cuda.empty_cache()
+    return res
 
 
 def type_map_section(ec, ctx, field, thr, steps, with_cpu, budget_s):
@@ -557,7 +634,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", type=int, default=0, help="testing only: edge of a smaller cube")
-    ap.add_argument("--batch-requests", type=int, default=256)
+    ap.add_argument("--batch-requests", type=int, default=4096)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-type-map", action="store_true")
     ap.add_argument("--profile-case", nargs="?", const="curve", choices=("curve", "typemap", "2d"),
@@ -667,7 +744,8 @@ def main():
                                                                                with_cpu=not args.no_cpu_baseline)
     type_map = None if (args.no_type_map or rank != 0) else type_map_section(
         ec, ctx, field, thr, 20, not args.no_cpu_baseline, args.cpu_budget)
-    batched = None if (args.no_batch or rank != 0) else batched_vs_per_field(ec, ctx, args.batch_requests)
+    batched = None if (args.no_batch or rank != 0) else config5_section(ec, ctx, args.batch_requests,
+                                                                         with_oracle=not args.no_cpu_baseline)
     frames = None if (args.no_batch or rank != 0) else realtime_frames_section(ec, ctx)
     streamed = None if (args.no_batch or rank != 0) else streamed_2048_section(ec, ctx)
 
@@ -697,7 +775,7 @@ def main():
         "config1": None if configs_2d is None else configs_2d.get("config1"),
         "config2": None if configs_2d is None else configs_2d.get("config2"),
         "type_map": type_map,
-        "batched_vs_per_field": batched,
+        "config5": batched,
         "realtime_frames": frames,
         "streamed_2048": streamed,
     }

@@ -109,8 +109,13 @@ int ec_ctx_destroy(ec_ctx *ctx);
  *  EC_OPT_AUTOTUNE: 1 = the first request of every shape class (ndim, dtype,
  *    level-count and size buckets, descriptors) times the candidate plans
  *    (tile depth, grid, schedule) on itself, synchronously, and later
- *    requests of the class use the fastest.  With the environment variable
- *    EC_AUTOTUNE_CACHE naming a file, tuned plans persist there as JSON.
+ *    requests of the class use the fastest.  ec_batch does the same per mix
+ *    class (field count, total cells, share of 3D cells, largest level count,
+ *    bucketed): the first batch of a class times its own launch plans (z
+ *    planes per 3D work item 16 / 32 / 64, rows per 2D item 32 / 64 / 128,
+ *    one or all resident blocks per SM) by coordinate descent.  With the
+ *    environment variable EC_AUTOTUNE_CACHE naming a file, tuned plans
+ *    persist there as JSON.
  *  EC_OPT_TEST_GIVE_UP (testing the failure path only): 1 = in the next 3D
  *    curve requests on the float32 TMA path, every block gives up its first
  *    bounded device wait at once, as if the staged plane had not arrived in
@@ -216,8 +221,16 @@ typedef struct {
 /* Curves of n independent fields of uneven sizes, dtypes and level counts in
  * one persistent-kernel launch (Sec. 4 notes that small images parallelise
  * poorly one at a time).  All pointers in `fields` are device pointers.
- * Results are identical to n separate ec_curve_2d / ec_curve_3d calls. */
+ * Results are identical to n separate ec_curve_2d / ec_curve_3d calls.
+ * With EC_OPT_AUTOTUNE the first batch of a mix class runs several times
+ * (synchronously) while its plan is chosen. */
 int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, void *stream);
+
+/* The plan the autotuner keeps for the mix class of `fields` (host array of
+ * n >= 1 descriptors; only ndim and dims are read): out = {z planes per 3D
+ * item, blocks per launch (0 = all resident), rows per 2D item};
+ * EC_ERR_ARG when the class is not tuned yet. */
+int ec_batch_tuned_plan(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, int32_t out[3]);
 
 /* ----------------------------------------------------- workload generator
  * The hash-box field of the low-memory workload (input generation only):
@@ -246,9 +259,12 @@ size_t ec_workspace_bytes(int dtype, int32_t ndim, const int64_t *dims, int32_t 
  * larger request) is admitted as a group; a group's inputs are copied in,
  * its curves computed by one batched launch (ec_batch) on the slot's own
  * stream and context, and its outputs copied back, so groups overlap on the
- * device.  Under light load a group is a single request.  Request fields,
- * thresholds and outputs are host pointers that must stay valid until the
- * request is done.                                                         */
+ * device.  Under light load a group is a single request.  A request field
+ * is a host pointer (copied in) or a device pointer (read in place, not
+ * counted in the budget); thresholds and outputs are host pointers.  All
+ * must stay valid until the request is done.  When `ctx` has
+ * EC_OPT_AUTOTUNE set at creation, the slots tune their groups' mix classes
+ * (as ec_batch does) into ctx's plans.                                     */
 typedef struct ec_server ec_server;
 int ec_server_create(ec_ctx *ctx, size_t device_mem_budget, int32_t max_slots, ec_server **server);
 /* Queue a request; *ticket identifies it.  EC_ERR_BUSY if the pending queue

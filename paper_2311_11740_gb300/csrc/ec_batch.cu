@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -411,6 +412,119 @@ struct BatchState {
 
 }  // namespace
 
+// Launch plan of one batch: z planes per 3D item, rows per ordinary 2D item,
+// blocks per launch (0 = as many as fit on every SM).
+struct BatchPlan {
+    int tz3 = 64;
+    int rows2d = 64;
+    int grid = 0;
+};
+
+static int batch_run(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, cudaStream_t s, const BatchPlan &plan);
+
+// Mix class of a batch for the autotuner: total cells (factor-4 buckets)
+// and share of 3D cells (quarters).
+static std::string batch_class_key(ec_ctx *ctx, const ec_field_desc *fields, int32_t n)
+{
+    double cells = 0, cells3 = 0;
+    for (int i = 0; i < n; i++) {
+        const ec_field_desc &d = fields[i];
+        const double c = d.ndim == 3 ? (double)d.dims[0] * d.dims[1] * d.dims[2] : (double)d.dims[0] * d.dims[1];
+        cells += c;
+        if (d.ndim == 3) cells3 += c;
+    }
+    char buf[96];
+    snprintf(buf, sizeof buf, "batch_sm%d_c%d_f%d", ctx->num_sms, (int)std::floor(std::log2(cells + 1) / 2),
+             (int)std::lround(4.0 * cells3 / std::max(cells, 1.0)));
+    return buf;
+}
+
+// Time one plan on the batch itself (one warm-up run, then the best of two).
+static int time_plan(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, cudaStream_t s, const BatchPlan &p,
+                     double &us)
+{
+    cudaEvent_t e0, e1;
+    EC_CUDA(cudaEventCreate(&e0));
+    EC_CUDA(cudaEventCreate(&e1));
+    us = 1e30;
+    int rc = EC_OK;
+    for (int rep = 0; rep < 3 && rc == EC_OK; rep++) {
+        cudaEventRecord(e0, s);
+        rc = batch_run(ctx, fields, n, s, p);
+        cudaEventRecord(e1, s);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = EC_ERR_CUDA; break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) us = std::min(us, (double)ms * 1e3);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+// Autotuner (EC_OPT_AUTOTUNE) for ec_batch: the first batch of a mix class
+// times candidate plans on itself by coordinate descent (3D item depth
+// 16 / 32 / 64, then 2D item rows 32 / 64 / 128, then one or all resident
+// blocks per SM), keeps the fastest per class with the single-field plans
+// (and in EC_AUTOTUNE_CACHE when set); later batches of the class use it.
+// Each candidate runs the whole batch, so the outputs end up written by the
+// last run as usual.
+// Every plan computes the same curves.
+static int tuned_batch_plan(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, cudaStream_t s, BatchPlan &plan)
+{
+    const std::string key = batch_class_key(ctx, fields, n);
+    int v[3];
+    if (tune_lookup(ctx, key, v)) {
+        plan.tz3 = v[0];
+        plan.grid = v[1];
+        plan.rows2d = v[2];
+        return EC_OK;
+    }
+    BatchPlan best = plan;
+    double best_us = 1e30;
+    auto consider = [&](BatchPlan p) -> int {
+        double us = 0;
+        const int rc = time_plan(ctx, fields, n, s, p, us);
+        if (rc == EC_OK && us < best_us) { best_us = us; best = p; }
+        return rc;
+    };
+    int rc = EC_OK;
+    for (int tz : {64, 32, 16}) {
+        BatchPlan p = best;
+        p.tz3 = tz;
+        if ((rc = consider(p))) return rc;
+    }
+    for (int rows : {32, 128}) {
+        BatchPlan p = best;
+        p.rows2d = rows;
+        if ((rc = consider(p))) return rc;
+    }
+    {
+        BatchPlan p = best;
+        p.grid = ctx->num_sms;
+        if ((rc = consider(p))) return rc;
+    }
+    plan = best;
+    const int w[3] = {best.tz3, best.grid, best.rows2d};
+    tune_store(ctx, key, w, best_us);
+    return EC_OK;
+}
+
+extern "C" int ec_batch_tuned_plan(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, int32_t out[3])
+{
+    clear_error();
+    if (!ctx || !fields || n < 1 || !out) { set_error("bad arguments"); return EC_ERR_ARG; }
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    int v[3];
+    if (!tune_lookup(ctx, batch_class_key(ctx, fields, n), v)) {
+        set_error("no tuned plan for this mix class yet");
+        return EC_ERR_ARG;
+    }
+    for (int i = 0; i < 3; i++) out[i] = v[i];
+    return EC_OK;
+}
+
 extern "C" int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, void *stream)
 {
     clear_error();
@@ -429,7 +543,17 @@ extern "C" int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, voi
     std::lock_guard<std::mutex> lock(ctx->mu);
     DeviceGuard dg(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
+    BatchPlan plan;
+    plan.grid = ctx->grid;
+    if (ctx->autotune && n > 0) {
+        const int rc = tuned_batch_plan(ctx, fields, n, s, plan);
+        if (rc) return rc;
+    }
+    return batch_run(ctx, fields, n, s, plan);
+}
 
+static int batch_run(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, cudaStream_t s, const BatchPlan &plan)
+{
     // ---- host tables: fields (largest first for scheduling) and items
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
@@ -469,10 +593,11 @@ extern "C" int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, voi
         int cnt = 0;
         if (d.ndim == 3) {
             F.dims[0] = d.dims[0]; F.dims[1] = d.dims[1]; F.dims[2] = d.dims[2];
-            for (int64_t z = 0; z < d.dims[0]; z += 64)
+            for (int64_t z = 0; z < d.dims[0]; z += plan.tz3)
                 for (int64_t y = 0; y < d.dims[1]; y += TYF)
                     for (int64_t x = 0; x < d.dims[2]; x += TXF) {
-                        items.push_back(BItem{f, (int)x, (int)y, (int)z, (int)std::min<int64_t>(z + 64, d.dims[0])});
+                        items.push_back(BItem{f, (int)x, (int)y, (int)z,
+                                              (int)std::min<int64_t>(z + plan.tz3, d.dims[0])});
                         cnt++;
                     }
         } else {
@@ -499,9 +624,10 @@ extern "C" int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, voi
                     cnt++;
                 }
             } else {
-                for (int64_t y = 0; y < d.dims[0]; y += 64)
+                for (int64_t y = 0; y < d.dims[0]; y += plan.rows2d)
                     for (int64_t x = 0; x < d.dims[1]; x += fast2d::SW) {
-                        items.push_back(BItem{f, (int)x, 0, (int)y, (int)std::min<int64_t>(y + 64, d.dims[0])});
+                        items.push_back(BItem{f, (int)x, 0, (int)y,
+                                              (int)std::min<int64_t>(y + plan.rows2d, d.dims[0])});
                         cnt++;
                     }
             }
@@ -514,10 +640,10 @@ extern "C" int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, voi
         const ec_field_desc &d = fields[i];
         int rc = ensure_scratch(ctx, curve_scratch_bytes(d.descriptors, d.L));
         if (rc) return rc;
-        CurvePlan plan;
-        plan.algo = ALGO_VOXEL;
-        plan.num_sms = ctx->num_sms;
-        rc = enqueue_curve(plan, 3, d.field, d.dims, d.dtype, d.thresholds, d.L, d.connectivity, d.descriptors, d.out,
+        CurvePlan cp;
+        cp.algo = ALGO_VOXEL;
+        cp.num_sms = ctx->num_sms;
+        rc = enqueue_curve(cp, 3, d.field, d.dims, d.dtype, d.thresholds, d.L, d.connectivity, d.descriptors, d.out,
                            ctx->ws, s);
         if (rc) return rc;
     }
@@ -565,7 +691,7 @@ extern "C" int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, voi
     int occ = 0;
     EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kThreads, smem));
     if (occ < 1) { set_error("batch kernel does not fit (%zu B shared)", smem); return EC_ERR_UNSUPPORTED; }
-    int grid = ctx->grid > 0 ? ctx->grid : ctx->num_sms * occ;
+    int grid = plan.grid > 0 ? std::min(plan.grid, ctx->num_sms * occ) : ctx->num_sms * occ;
     grid = std::min<int>(grid, (int)items.size());
 
     // ---- capture the sequence into a graph; update the cached executable if possible

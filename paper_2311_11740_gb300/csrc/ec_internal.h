@@ -166,6 +166,13 @@ int ensure_scratch(ec_ctx *ctx, size_t bytes);
 int tuned_plan(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int dtype, const void *thr,
                int32_t L, int connectivity, uint32_t desc, int64_t *out, cudaStream_t s, CurvePlan &plan);
 void tune_release(ec_ctx *ctx);
+// `to` uses (and adds to) the tuned plans of `from` from now on; called with
+// from->mu held, before `to` is used.
+void tune_share(ec_ctx *from, ec_ctx *to);
+// Plans kept by the tuner under other keys (ec_batch's mix classes): three
+// integers and the time they took.  Called with ctx->mu held.
+bool tune_lookup(ec_ctx *ctx, const std::string &key, int out[3]);
+void tune_store(ec_ctx *ctx, const std::string &key, const int v[3], double us);
 // Free what ec_batch keeps in a context.
 void batch_release(ec_ctx *ctx);
 void stream_release(ec_ctx *ctx);

@@ -314,6 +314,12 @@ int ec_server_create(ec_ctx *ctx, size_t device_mem_budget, int32_t max_slots, e
             break;
         }
         if ((rc = ec_ctx_create(&sl.bctx, ctx->device)) != EC_OK) break;
+        if (ctx->autotune) {
+            // the slots tune their groups' mix classes into the creator's plans
+            std::lock_guard<std::mutex> lock(ctx->mu);
+            sl.bctx->autotune = ctx->autotune;
+            tune_share(ctx, sl.bctx);
+        }
     }
     if (rc != EC_OK) {
         for (auto &sl : sv->slots) {

@@ -6,8 +6,9 @@
 // CUDA events on the request's stream.  Results are cached in the context and,
 // when the environment variable EC_AUTOTUNE_CACHE names a file, kept in that
 // JSON file (one object: class key -> [tile_z, grid, schedule, microseconds])
-// across processes.  Every candidate computes the same curves, so tuning
-// changes only speed.
+// across processes.  A server's slot contexts share the tuned plans of the
+// context the server was created on.  Every candidate computes the same
+// curves, so tuning changes only speed.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -16,6 +17,7 @@
 
 #include <cmath>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -31,8 +33,10 @@ struct TunedPlan {
 };
 
 struct TuneCache {
+    std::mutex mu;   // guards plans and refs (contexts sharing a cache have separate locks)
     std::map<std::string, TunedPlan> plans;
     bool loaded = false;
+    int refs = 1;
 };
 
 std::string class_key(int device_sms, int ndim, int dtype, int32_t L, uint32_t desc, const int64_t *dims)
@@ -90,10 +94,13 @@ void save_file(const TuneCache &tc)
     rename(tmp.c_str(), path);
 }
 
+// The context's cache, created on first use (under ctx->mu); lock tc.mu
+// before touching its plans.
 TuneCache &cache_of(ec_ctx *ctx)
 {
     if (!ctx->tune_cache) ctx->tune_cache = new TuneCache();
     TuneCache &tc = *(TuneCache *)ctx->tune_cache;
+    std::lock_guard<std::mutex> g(tc.mu);
     if (!tc.loaded) load_file(tc);
     return tc;
 }
@@ -107,12 +114,15 @@ int ec::tuned_plan(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims
 {
     TuneCache &tc = cache_of(ctx);
     const std::string key = class_key(ctx->num_sms, ndim, dtype, L, desc, dims);
-    auto it = tc.plans.find(key);
-    if (it != tc.plans.end()) {
-        plan.tile_z = it->second.tile_z;
-        plan.grid = it->second.grid;
-        plan.hist_schedule = it->second.schedule;
-        return EC_OK;
+    {
+        std::lock_guard<std::mutex> g(tc.mu);
+        auto it = tc.plans.find(key);
+        if (it != tc.plans.end()) {
+            plan.tile_z = it->second.tile_z;
+            plan.grid = it->second.grid;
+            plan.hist_schedule = it->second.schedule;
+            return EC_OK;
+        }
     }
     std::vector<TunedPlan> cands;
     if (ndim == 3) {
@@ -155,18 +165,56 @@ int ec::tuned_plan(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    tc.plans[key] = best;
-    save_file(tc);
+    {
+        std::lock_guard<std::mutex> g(tc.mu);
+        tc.plans[key] = best;
+        save_file(tc);
+    }
     plan.tile_z = best.tile_z;
     plan.grid = best.grid;
     plan.hist_schedule = best.schedule;
     return EC_OK;
 }
 
+bool ec::tune_lookup(ec_ctx *ctx, const std::string &key, int out[3])
+{
+    TuneCache &tc = cache_of(ctx);
+    std::lock_guard<std::mutex> g(tc.mu);
+    auto it = tc.plans.find(key);
+    if (it == tc.plans.end()) return false;
+    out[0] = it->second.tile_z;
+    out[1] = it->second.grid;
+    out[2] = it->second.schedule;
+    return true;
+}
+
+void ec::tune_store(ec_ctx *ctx, const std::string &key, const int v[3], double us)
+{
+    TuneCache &tc = cache_of(ctx);
+    std::lock_guard<std::mutex> g(tc.mu);
+    tc.plans[key] = TunedPlan{v[0], v[1], v[2], us};
+    save_file(tc);
+}
+
+void ec::tune_share(ec_ctx *from, ec_ctx *to)
+{
+    TuneCache &tc = cache_of(from);
+    std::lock_guard<std::mutex> g(tc.mu);
+    tc.refs++;
+    to->tune_cache = &tc;
+}
+
 void ec::tune_release(ec_ctx *ctx)
 {
-    delete (TuneCache *)ctx->tune_cache;
+    TuneCache *tc = (TuneCache *)ctx->tune_cache;
     ctx->tune_cache = nullptr;
+    if (!tc) return;
+    bool last;
+    {
+        std::lock_guard<std::mutex> g(tc->mu);
+        last = --tc->refs == 0;
+    }
+    if (last) delete tc;
 }
 
 extern "C" int ec_tuned_plan(ec_ctx *ctx, int32_t ndim, int dtype, int32_t L, uint32_t descriptors,
@@ -176,6 +224,7 @@ extern "C" int ec_tuned_plan(ec_ctx *ctx, int32_t ndim, int dtype, int32_t L, ui
     if (!ctx || !dims || !out || (ndim != 2 && ndim != 3)) { set_error("bad arguments"); return EC_ERR_ARG; }
     std::lock_guard<std::mutex> lock(ctx->mu);
     TuneCache &tc = cache_of(ctx);
+    std::lock_guard<std::mutex> g(tc.mu);
     auto it = tc.plans.find(class_key(ctx->num_sms, ndim, dtype, L, descriptors, dims));
     if (it == tc.plans.end()) { set_error("no tuned plan for this class yet"); return EC_ERR_ARG; }
     out[0] = it->second.tile_z;

@@ -65,6 +65,7 @@ def lib():
             L.ec_curve_3d_stream.argtypes = [P, P, SLAB_FN, P, ctypes.POINTER(I64), ctypes.c_int, P, I32,
                                              ctypes.c_int, U32, I64, ctypes.c_size_t, P]
             L.ec_batch.argtypes = [P, ctypes.POINTER(FieldDesc), I32, P]
+            L.ec_batch_tuned_plan.argtypes = [P, ctypes.POINTER(FieldDesc), I32, ctypes.POINTER(I32)]
             L.ec_workspace_bytes.argtypes = [ctypes.c_int, I32, ctypes.POINTER(I64), I32, U32]
             L.ec_workspace_bytes.restype = ctypes.c_size_t
             L.ec_vertex_table_2d.argtypes = [P]
@@ -254,26 +255,47 @@ def _desc(field, thresholds, L, connectivity, descriptors, out) -> FieldDesc:
     return d
 
 
+class Batch:
+    """A batch of fields (dicts {field, thresholds, L, connectivity,
+    descriptors} with CUDA tensors) with its int64 CUDA outputs allocated
+    once; run() calls ec_batch on it and may be repeated."""
+
+    def __init__(self, fields, ctx: Context | None = None):
+        import torch
+        self.dev = fields[0]["field"].device.index or 0
+        self.ctx = ctx or default_context(self.dev)
+        self.fields = fields
+        self.outs, descs = [], []
+        for f in fields:
+            L = f.get("L") or f["thresholds"].numel()
+            o = torch.empty((n_rows(f.get("descriptors", 1)), L), dtype=torch.int64, device=f["field"].device)
+            self.outs.append(o)
+            descs.append(_desc(f["field"], f.get("thresholds"), L, f.get("connectivity"), f.get("descriptors", 1),
+                               o))
+        self.arr = (FieldDesc * len(descs))(*descs)
+
+    def run(self, stream=None):
+        _check(lib().ec_batch(self.ctx.handle, self.arr, len(self.arr), _stream_ptr(stream, self.dev)))
+        return self.outs
+
+    def tuned_plan(self):
+        """(3D item depth, grid, 2D item rows) the autotuner keeps for this
+        batch's mix class, or None if it has none."""
+        out = (ctypes.c_int32 * 3)()
+        rc = lib().ec_batch_tuned_plan(self.ctx.handle, self.arr, len(self.arr), out)
+        return None if rc != 0 else tuple(out)
+
+
 def batch(fields, ctx: Context | None = None, stream=None):
     """ec_batch over a list of dicts {field, thresholds, L, connectivity,
     descriptors} with CUDA tensors; returns the list of int64 CUDA outputs."""
-    import torch
-    dev = fields[0]["field"].device.index or 0
-    ctx = ctx or default_context(dev)
-    outs, descs = [], []
-    for f in fields:
-        L = f.get("L") or f["thresholds"].numel()
-        o = torch.empty((n_rows(f.get("descriptors", 1)), L), dtype=torch.int64, device=f["field"].device)
-        outs.append(o)
-        descs.append(_desc(f["field"], f.get("thresholds"), L, f.get("connectivity"), f.get("descriptors", 1), o))
-    arr = (FieldDesc * len(descs))(*descs)
-    _check(lib().ec_batch(ctx.handle, arr, len(descs), _stream_ptr(stream, dev)))
-    return outs
+    return Batch(fields, ctx).run(stream)
 
 
 class Server:
-    """The continuous-batching request loop (ec_server_*).  Requests use host
-    numpy arrays; outputs are host numpy arrays filled when done."""
+    """The continuous-batching request loop (ec_server_*).  Request fields are
+    host arrays / CPU tensors (copied in) or CUDA tensors (read in place);
+    outputs are host numpy arrays filled when done."""
 
     def __init__(self, device_mem_budget: int, max_slots: int = 8, ctx: Context | None = None, device: int = 0):
         self.ctx = ctx or default_context(device)
@@ -288,7 +310,7 @@ class Server:
             field = field.contiguous()
         if thresholds is not None:
             if hasattr(thresholds, "data_ptr"):
-                thresholds = thresholds.contiguous().numpy()
+                thresholds = thresholds.detach().contiguous().cpu().numpy()
             thresholds = np.ascontiguousarray(thresholds, dtype=_NP_DTYPES[dtype_code(field)])
             L = thresholds.size if L is None else L
         out = np.zeros((n_rows(descriptors), L), dtype=np.int64)

@@ -173,6 +173,41 @@ def request_stream(seed: int = 5, n: int = 4096, rho_rate: float = 1000.0, max_2
     return reqs
 
 
+def _blur_fft32(f: torch.Tensor, sigma: float) -> torch.Tensor:
+    """Periodic Gaussian blur by a real FFT in float32 (device fields)."""
+    dims = tuple(range(f.dim()))
+    freqs = [torch.fft.fftfreq(n, device=f.device) for n in f.shape[:-1]]
+    freqs.append(torch.fft.rfftfreq(f.shape[-1], device=f.device))
+    c = -2 * (math.pi ** 2) * (sigma ** 2)
+    H = None
+    for a, w in enumerate(freqs):   # separable: product of 1D factors
+        shp = [1] * f.dim()
+        shp[a] = -1
+        h = torch.exp(c * w * w).view(shp)
+        H = h if H is None else H * h
+    return torch.fft.irfftn(torch.fft.rfftn(f, dim=dims) * H, s=f.shape, dim=dims)
+
+
+def request_field_device(req: dict, device="cuda"):
+    """One request's field generated on the device: float32 N(0,1) noise from
+    a device generator seeded with the request's seed on the power-of-two
+    box that holds the field, smoothed by a periodic Gaussian (sigma) through
+    a float32 FFT and cropped to the field (so a stream of uneven sizes needs
+    only a few FFT plans); 2D fields are quantised to uint8, 3D fields get L
+    uniform float32 thresholds over [min, max].  Same recipe as
+    request_field, other random numbers (the device generator)."""
+    g = torch.Generator(device=device)
+    g.manual_seed(int(req["seed"]))
+    side = req["side"]
+    box = 1 << max(0, (side - 1).bit_length())
+    f = _blur_fft32(torch.randn((box,) * req["ndim"], generator=g, dtype=torch.float32, device=device), req["sigma"])
+    f = f[(slice(0, side),) * req["ndim"]].contiguous()
+    if req["ndim"] == 2:
+        return quantize_u8(f), None
+    thr = uniform_thresholds(f.min().item(), f.max().item(), req["L"], device=device)
+    return f.contiguous(), thr
+
+
 def request_field(req: dict, device="cpu"):
     """Materialise one request's field (and thresholds for float32 fields)."""
     if req["ndim"] == 2:
