@@ -161,6 +161,7 @@ __device__ void item_3d(const BField &F, const BItem &it, const Shared &S, const
     c.bin3 = ~0u;
     c.x0 = it.x0; c.y0 = it.y0; c.z0 = it.z0; c.z1 = it.z1;
     c.interior = c.x0 >= 4 && c.x0 + TXF + 4 <= c.p.W;
+    c.skip = c.x0 + TXF > c.p.W || c.y0 + TYF > c.p.H;
     c.base = 0;
     c.parity = 0;
     c.inflight = 0;

@@ -114,9 +114,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_pixel2d_fast(Params p)
         c.y1 = (int)min((int64_t)c.y0 + p.ry, p.H);
         c.interior = c.x0 >= 2 && c.x0 + SW + 2 <= p.W;
         __syncthreads();   // ring reuse across items
-        if constexpr (ROWS == ROWS_ALIGNED) walk_item_2d_async<T, CONN4, DM, fast3d::STG_ALIGNED>(c, win);
-        else if constexpr (ROWS == ROWS_COVER) walk_item_2d_async<T, CONN4, DM, fast3d::STG_COVER>(c, win);
-        else walk_item_2d<T, CONN4, DM>(c, win);
+        // a strip whose counted columns reach past the field leaves out the
+        // pixels at level L (the generic descriptor path always does)
+        if (DM != 0 && c.x0 + SW > p.W) {
+            if constexpr (ROWS == ROWS_ALIGNED) walk_item_2d_async<T, CONN4, DM, fast3d::STG_ALIGNED, false, true>(c, win);
+            else if constexpr (ROWS == ROWS_COVER) walk_item_2d_async<T, CONN4, DM, fast3d::STG_COVER, false, true>(c, win);
+            else walk_item_2d<T, CONN4, DM, true>(c, win);
+        } else {
+            if constexpr (ROWS == ROWS_ALIGNED) walk_item_2d_async<T, CONN4, DM, fast3d::STG_ALIGNED>(c, win);
+            else if constexpr (ROWS == ROWS_COVER) walk_item_2d_async<T, CONN4, DM, fast3d::STG_COVER>(c, win);
+            else walk_item_2d<T, CONN4, DM>(c, win);
+        }
     }
     if (c.sh_hist) {
         __syncthreads();

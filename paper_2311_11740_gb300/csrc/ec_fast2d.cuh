@@ -137,8 +137,12 @@ template <int DM, int D>
 constexpr int dm_row2() { return ((DM & 1) && D > 0) + ((DM & 2) && D > 1); }
 
 // Load row y+1 into window slot (R+1)%3 (R = position of row y) and count
-// row y if it belongs to the item.
-template <typename T, bool CONN4, int R, int DM>
+// row y if it belongs to the item.  SKIP (strips whose counted columns reach
+// past the field): pixels at the never-active level L are left out of the
+// compile-time-descriptor histogram, as the generic path always does; their
+// changes belong to the discarded level L, and past the field's edge they
+// would all hit one word and serialise the warp's atomics.
+template <typename T, bool CONN4, int R, int DM, bool SKIP = false>
 __device__ __forceinline__ void count_row(Ctx2<T> &c, uint32_t (&win)[3][5], int y)
 {
     {
@@ -173,6 +177,7 @@ __device__ __forceinline__ void count_row(Ctx2<T> &c, uint32_t (&win)[3][5], int
             int *const h = c.sh_hist;
 #pragma unroll
             for (int v = 0; v < 4; v++) {
+                if (SKIP && key[v] >= (uint32_t)L) continue;
                 int *const e = h + key[v] * ND;
                 if (DM & 1) atomicAdd(e + dm_row2<DM, 0>(), ecv[v]);
                 if (DM & 2) atomicAdd(e + dm_row2<DM, 1>(), pev[v]);
@@ -201,14 +206,14 @@ __device__ __forceinline__ void count_row(Ctx2<T> &c, uint32_t (&win)[3][5], int
 // start the loads of row y+2, then (after the barrier) load row y+1 into
 // window slot (R+1)%3 with R = t mod 3 and count row y if it belongs to the
 // item.  Rows y0-1 .. y1 pass through the window.
-template <typename T, bool CONN4, int R, int DM>
+template <typename T, bool CONN4, int R, int DM, bool SKIP = false>
 __device__ __forceinline__ void ystep(Ctx2<T> &c, uint32_t (&win)[3][5], RowRaw<T> &raw, int t)
 {
     const int y = c.y0 - 2 + t;
     bin_row<T>(c, y + 1, raw);
     if (y + 2 <= c.y1) load_row<T>(c, y + 2, raw);
     __syncthreads();
-    count_row<T, CONN4, R, DM>(c, win, y);
+    count_row<T, CONN4, R, DM, SKIP>(c, win, y);
 }
 
 // ---- asynchronous path: rows copied to shared memory KA rows ahead with
@@ -338,7 +343,7 @@ __device__ __forceinline__ void bin_row_raw(Ctx2<T> &c, int64_t y)
 // Asynchronous row step, y = y0 - 2 + t: bin row y+1 (its copies finished
 // before the previous barrier), start the copies of row y+2+KA, wait for
 // this thread's copies of row y+2, synchronise, then count as ystep does.
-template <typename T, bool CONN4, int R, int DM, int STG, bool BANDED>
+template <typename T, bool CONN4, int R, int DM, int STG, bool BANDED, bool SKIP = false>
 __device__ __forceinline__ void ystep_async(Ctx2<T> &c, uint32_t (&win)[3][5], int t)
 {
     const int y = c.y0 - 2 + t;
@@ -346,25 +351,25 @@ __device__ __forceinline__ void ystep_async(Ctx2<T> &c, uint32_t (&win)[3][5], i
     copy_row<T, STG, BANDED>(c, y + 2 + KA, y + 2 + KA <= c.y1);
     cp_async_wait<KA>();
     __syncthreads();
-    count_row<T, CONN4, R, DM>(c, win, y);
+    count_row<T, CONN4, R, DM, SKIP>(c, win, y);
 }
 
 // Walk one item: rows y0-1 .. y1 are binned, rows y0 .. y1-1 counted.
-template <typename T, bool CONN4, int DM>
+template <typename T, bool CONN4, int DM, bool SKIP = false>
 __device__ __forceinline__ void walk_item_2d(Ctx2<T> &c, uint32_t (&win)[3][5])
 {
     RowRaw<T> raw;
     load_row<T>(c, c.y0 - 1, raw);
     const int nsteps = c.y1 - c.y0 + 2;
     for (int t = 0; t < nsteps; t += 3) {
-        ystep<T, CONN4, 0, DM>(c, win, raw, t);
-        if (t + 1 < nsteps) ystep<T, CONN4, 1, DM>(c, win, raw, t + 1);
-        if (t + 2 < nsteps) ystep<T, CONN4, 2, DM>(c, win, raw, t + 2);
+        ystep<T, CONN4, 0, DM, SKIP>(c, win, raw, t);
+        if (t + 1 < nsteps) ystep<T, CONN4, 1, DM, SKIP>(c, win, raw, t + 1);
+        if (t + 2 < nsteps) ystep<T, CONN4, 2, DM, SKIP>(c, win, raw, t + 2);
     }
 }
 
 // Asynchronous walk of one item (same rows as walk_item_2d).
-template <typename T, bool CONN4, int DM, int STG, bool BANDED = false>
+template <typename T, bool CONN4, int DM, int STG, bool BANDED = false, bool SKIP = false>
 __device__ __forceinline__ void walk_item_2d_async(Ctx2<T> &c, uint32_t (&win)[3][5])
 {
     for (int q = 0; q <= KA; q++) copy_row<T, STG, BANDED>(c, c.y0 - 1 + q, c.y0 - 1 + q <= c.y1);
@@ -372,9 +377,9 @@ __device__ __forceinline__ void walk_item_2d_async(Ctx2<T> &c, uint32_t (&win)[3
     __syncthreads();
     const int nsteps = c.y1 - c.y0 + 2;
     for (int t = 0; t < nsteps; t += 3) {
-        ystep_async<T, CONN4, 0, DM, STG, BANDED>(c, win, t);
-        if (t + 1 < nsteps) ystep_async<T, CONN4, 1, DM, STG, BANDED>(c, win, t + 1);
-        if (t + 2 < nsteps) ystep_async<T, CONN4, 2, DM, STG, BANDED>(c, win, t + 2);
+        ystep_async<T, CONN4, 0, DM, STG, BANDED, SKIP>(c, win, t);
+        if (t + 1 < nsteps) ystep_async<T, CONN4, 1, DM, STG, BANDED, SKIP>(c, win, t + 1);
+        if (t + 2 < nsteps) ystep_async<T, CONN4, 2, DM, STG, BANDED, SKIP>(c, win, t + 2);
     }
     cp_async_wait<0>();
 }

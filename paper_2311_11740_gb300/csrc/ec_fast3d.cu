@@ -188,6 +188,7 @@ k_voxel3d_fast(const __grid_constant__ CUtensorMap tmap, Params p)
         c.z0 = p.zc0 + bz * p.tz;
         c.z1 = min(c.z0 + p.tz, p.zc1);
         c.interior = c.x0 >= 4 && c.x0 + TXF + 4 <= p.W;
+        c.skip = c.x0 + TXF > p.W || c.y0 + TYF > p.H;
         __syncthreads();   // the previous item is done with both rings
         c.base = seq;
         if constexpr (SLICE) {

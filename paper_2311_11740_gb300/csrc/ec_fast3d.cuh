@@ -237,6 +237,11 @@ struct Ctx {
     uint32_t parity;
     uint32_t inflight;         // thread 0: ring slots with a TMA copy issued and not yet waited for
     bool interior;
+    // the item's counted box reaches past the field: voxels at the
+    // never-active level L are left out of the interleaved histogram (their
+    // changes belong to the discarded level; past the edge they would all hit
+    // one word and serialise the warp's atomics)
+    bool skip;
 };
 
 template <typename T>
@@ -515,6 +520,7 @@ __device__ __forceinline__ void count_plane(Ctx<T> &c, uint32_t (&win)[3][3][5],
                 constexpr int ND = dm_nd<DM>();
 #pragma unroll
                 for (int v = 0; v < 4; v++) {
+                    if (c.skip && key[v] >= (uint32_t)L) continue;
                     int *const e = h + key[v] * ND;
                     if (DM & 1) atomicAdd(e + dm_row<DM, 0>(), ecv[v]);
                     if (DM & 2) atomicAdd(e + dm_row<DM, 1>(), pev[v]);
@@ -826,9 +832,10 @@ __device__ __forceinline__ void load_rows5(const Ctx<T> &c, int plane, Row5 (&W)
 // voxels 0, 1 and kd = voxels 2, 3).  Histogram rows interleaved per level,
 // [L+1][nd], with the never-active level L in its own (discarded) slot.
 // DM != 0: descriptor rows fixed at compile time; DM == 0: rows[] at run time.
+// skip: voxels at level L are left out (items reaching past the field).
 template <int DM>
 __device__ __forceinline__ void slice_hist(int *h, int nd, const int (&rows)[kMaxDesc], uint32_t kb, uint32_t kd,
-                                           const SliceOut &o)
+                                           const SliceOut &o, bool skip, uint32_t L)
 {
     const uint32_t key[4] = {kb & 0xFFFFu, kb >> 16, kd & 0xFFFFu, kd >> 16};
     const int ecv[4] = {sbyte<0>(o.ec), sbyte<1>(o.ec), sbyte<2>(o.ec), sbyte<3>(o.ec)};
@@ -836,6 +843,7 @@ __device__ __forceinline__ void slice_hist(int *h, int nd, const int (&rows)[kMa
         constexpr int ND = dm_nd<DM>();
 #pragma unroll
         for (int v = 0; v < 4; v++) {
+            if (skip && key[v] >= L) continue;
             int *const e = h + key[v] * ND;
             if (DM & 1) atomicAdd(e + dm_row<DM, 0>(), ecv[v]);
             if (DM & 2) {
@@ -853,6 +861,7 @@ __device__ __forceinline__ void slice_hist(int *h, int nd, const int (&rows)[kMa
         const int av[4] = {sbyte<0>(o.area), sbyte<1>(o.area), sbyte<2>(o.area), sbyte<3>(o.area)};
 #pragma unroll
         for (int v = 0; v < 4; v++) {
+            if (skip && key[v] >= L) continue;
             int *const e = h + key[v] * nd;
             if (rows[0] >= 0) atomicAdd(e + rows[0], ecv[v]);
             if (rows[1] >= 0) atomicAdd(e + rows[1], pv[v]);
@@ -874,7 +883,7 @@ __device__ __forceinline__ void slice_step(Ctx<T> &c, Row5 (&P)[3], Row5 (&Q)[3]
     } else if (h >= c.z0) {
         constexpr bool AREA = DM == 0 || (DM & 4) != 0;
         const SliceOut o = slice_quad<AREA, PER>(P, Q, st);
-        slice_hist<DM>(c.sh_hist, c.p.nd, c.p.rows, P[1].b, P[1].d, o);
+        slice_hist<DM>(c.sh_hist, c.p.nd, c.p.rows, P[1].b, P[1].d, o, c.skip, (uint32_t)c.p.L);
     }
 }
 

@@ -286,15 +286,19 @@ __device__ __forceinline__ void load_rows(const Ctx &c, int plane, Row5 (&W)[4])
 }
 
 // Add one quad's changes at its levels (key pairs kb = voxels 0, 1 and
-// kd = voxels 2, 3).
-template <typename T, int DM>
-__device__ __forceinline__ void add_quad(int *h, uint32_t kb, uint32_t kd, const SliceOut &o)
+// kd = voxels 2, 3).  SKIP (items whose counted box reaches past the field):
+// voxels at the never-active level L are left out.  Their changes belong to
+// the discarded level L, and outside the field they would all hit the same
+// word and serialise the warp's atomics.
+template <typename T, int DM, bool SKIP>
+__device__ __forceinline__ void add_quad(int *h, uint32_t kb, uint32_t kd, const SliceOut &o, uint32_t L)
 {
     constexpr int hw = HW<T>();
     const uint32_t key[4] = {kb & 0xFFFFu, kb >> 16, kd & 0xFFFFu, kd >> 16};
     const int ecv[4] = {sbyte<0>(o.ec), sbyte<1>(o.ec), sbyte<2>(o.ec), sbyte<3>(o.ec)};
 #pragma unroll
     for (int v = 0; v < 4; v++) {
+        if (SKIP && key[v] >= L) continue;
         int *const e = h + key[v];
         atomicAdd(e + R_EC * hw, ecv[v]);
         if (DM & 4) {
@@ -327,9 +331,9 @@ __device__ __forceinline__ void flush_packed(int *h, int L)
     }
 }
 
-template <typename T, int DM>
+template <typename T, int DM, bool SKIP>
 __device__ __forceinline__ void half_step(Ctx &c, int *hist, Row5 (&P)[4], Row5 (&Q)[4], SliceState &sa,
-                                          SliceState &sb, int h)
+                                          SliceState &sb, int h, uint32_t L)
 {
     constexpr bool PER = (DM & 2) != 0;
     if (h >= c.z0 - 2) load_rows(c, h + 1, Q);
@@ -338,9 +342,31 @@ __device__ __forceinline__ void half_step(Ctx &c, int *hist, Row5 (&P)[4], Row5 
     } else if (h >= c.z0) {
         SliceOut oa, ob;
         slice_pair<(DM & 4) ? AREA_FREE_FACES : AREA_NONE, PER>(P, Q, sa, sb, oa, ob);
-        add_quad<T, DM>(hist, P[1].b, P[1].d, oa);
-        add_quad<T, DM>(hist, P[2].b, P[2].d, ob);
+        add_quad<T, DM, SKIP>(hist, P[1].b, P[1].d, oa, L);
+        add_quad<T, DM, SKIP>(hist, P[2].b, P[2].d, ob, L);
     }
+}
+
+// The plane walk of one item (z0-4 .. z1-1 in barrier steps of two planes).
+// False when a bounded wait gave up (the block then returns).
+template <typename T, int DM, bool SKIP>
+__device__ __forceinline__ bool walk_item(Ctx &c, const CUtensorMap *tmap, int *hist, Row5 (&W0)[4],
+                                          Row5 (&W1)[4], SliceState &sa, SliceState &sb, uint32_t &nbar, int L)
+{
+    const int nsteps = c.z1 - c.z0 + 4;
+    for (int t = 0; t < nsteps; t += 2) {
+        const int h = c.z0 - 4 + t;
+        if (!barrier_step<T>(c, tmap, h, L)) return false;
+        if (DM & 4) {
+            if (++nbar == 3) {
+                nbar = 0;
+                flush_packed<T>(hist, L);
+            }
+        }
+        half_step<T, DM, SKIP>(c, hist, W0, W1, sa, sb, h, (uint32_t)L);
+        if (t + 1 < nsteps) half_step<T, DM, SKIP>(c, hist, W1, W0, sa, sb, h + 1, (uint32_t)L);
+    }
+    return true;
 }
 
 template <typename T, int DM>
@@ -416,19 +442,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_planar3d(const __grid_constant_
                 issue_plane<T>(c, &tmap, pz);
             }
         }
-        const int nsteps = c.z1 - c.z0 + 4;
-        for (int t = 0; t < nsteps; t += 2) {
-            const int h = c.z0 - 4 + t;
-            if (!barrier_step<T>(c, &tmap, h, L)) return;
-            if (DM & 4) {
-                if (++nbar == 3) {
-                    nbar = 0;
-                    flush_packed<T>(hist, L);
-                }
-            }
-            half_step<T, DM>(c, hist, W0, W1, sa, sb, h);
-            if (t + 1 < nsteps) half_step<T, DM>(c, hist, W1, W0, sa, sb, h + 1);
-        }
+        // counted voxels x0 .. x0+63, y0 .. y0+31: past the field's edge the
+        // walk leaves out voxels at level L
+        const bool skip = c.x0 + TX > p.W || c.y0 + TY > p.H;
+        const bool ok = skip ? walk_item<T, DM, true>(c, &tmap, hist, W0, W1, sa, sb, nbar, L)
+                             : walk_item<T, DM, false>(c, &tmap, hist, W0, W1, sa, sb, nbar, L);
+        if (!ok) return;
         seq += (uint32_t)(c.z1 - c.z0 + 2);
     }
     __syncthreads();
