@@ -576,7 +576,7 @@ def streamed_2048_section(ec, ctx, n=2048, cap=4 << 30):
         vox = n ** 3
         peak, peak_kind = measured_peaks()
         ok = bool(got[0, -1] == 1 and got[1, -1] == vox and np.all(np.diff(got[1]) >= 0))
-        return {"workload": f"{n}^3 uint16 hash-box field (seed 4, 5^3 box of a SplitMix64 hash), 4096 identity "
+        return {"workload": f"{n}^3 uint16 hash-box field (seed 4, 5^3 box of a MurmurHash3-finaliser counter hash), 4096 identity "
                             f"levels, EC+volume, 64-plane slabs generated on the device, {cap >> 30} GB cap",
                 "ms_per_pass": dt * 1e3, "value": vox / dt / 1e9, "unit": "Gvoxels/s",
                 "histogram_kernel_ms": kms, "histogram_launches": kl,

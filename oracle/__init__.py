@@ -180,7 +180,7 @@ def ec_curves(field: np.ndarray, thresholds, L: int, connectivity: int, descript
 
 def hashbox_u16(seed: int, x0: int, y0: int, z0: int, nx: int, ny: int, nz: int) -> np.ndarray:
     """The hash-box field of the low-memory workload, regenerated on the CPU
-    (SplitMix64 counter hash smoothed by a 5^3 box), shape (nz, ny, nx)."""
+    (MurmurHash3-finaliser counter hash smoothed by a 5^3 box), shape (nz, ny, nx)."""
     out = np.empty((nz, ny, nx), dtype=np.uint16)
     rc = _load().oracle_hashbox_u16(seed, x0, y0, z0, nx, ny, nz, _ptr(out))
     if rc != 0:

@@ -405,30 +405,32 @@ int oracle_ec_dual_2d(const int32_t *bins, int64_t h, int64_t w, int32_t L, int6
 /* ------------------------------------------- hash-box field (workload input)
  *
  * Counter-based generator for the low-memory streaming workload, implemented
- * here on its own from the published SplitMix64 definition (Steele, Lea and
- * Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014:
- * z += 0x9E3779B97F4A7C15; z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9;
- * z = (z ^ (z >> 27)) * 0x94D049BB133111EB; z ^= z >> 31).
+ * here on its own from the published MurmurHash3 32-bit finaliser (Austin
+ * Appleby, MurmurHash3, public domain: u ^= u >> 16; u *= 0x85EBCA6B;
+ * u ^= u >> 13; u *= 0xC2B2AE35; u ^= u >> 16), called m below.
  *
- * h(x,y,z) = low 16 bits of SplitMix64 applied to the counter
- *            seed*2^48 ^ (z mod 2^16)*2^32 ^ (y mod 2^16)*2^16 ^ (x mod 2^16)
+ * a        = m(lo32(seed) ^ m(hi32(seed)))
+ * h(x,y,z) = low 16 bits of m(m(m(a ^ z) ^ y) ^ x)      (x, y, z mod 2^32)
  * v(x,y,z) = floor( sum_{|dx|,|dy|,|dz| <= 2} h(x+dx, y+dy, z+dz) * 4096
  *                   / (125 * 65536) )                       in [0, 4095]
  * defined for all integer coordinates (no border case).
  */
-static uint64_t splitmix64(uint64_t z)
+static uint32_t murmur_fmix32(uint32_t u)
 {
-    z += 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
+    u ^= u >> 16;
+    u *= 0x85EBCA6Bu;
+    u ^= u >> 13;
+    u *= 0xC2B2AE35u;
+    u ^= u >> 16;
+    return u;
 }
 
 static uint32_t hash16(uint64_t seed, int64_t x, int64_t y, int64_t z)
 {
-    uint64_t ctr = (seed << 48) ^ (((uint64_t)z & 0xFFFFull) << 32)
-                 ^ (((uint64_t)y & 0xFFFFull) << 16) ^ ((uint64_t)x & 0xFFFFull);
-    return (uint32_t)(splitmix64(ctr) & 0xFFFFull);
+    const uint32_t a = murmur_fmix32((uint32_t)seed ^ murmur_fmix32((uint32_t)(seed >> 32)));
+    const uint32_t hz = murmur_fmix32(a ^ (uint32_t)z);
+    const uint32_t hy = murmur_fmix32(hz ^ (uint32_t)y);
+    return murmur_fmix32(hy ^ (uint32_t)x) & 0xFFFFu;
 }
 
 int oracle_hashbox_u16(uint64_t seed, int64_t x0, int64_t y0, int64_t z0,

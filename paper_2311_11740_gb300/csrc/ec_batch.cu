@@ -409,6 +409,7 @@ struct BatchState {
     size_t staging_bytes = 0;
     cudaEvent_t staged_free = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;   // capture-time branch of the planar launches
 };
 
 }  // namespace
@@ -419,6 +420,8 @@ struct BatchPlan {
     int tz3 = 64;
     int rows2d = 64;
     int grid = 0;
+    int64_t planar_min = int64_t(1) << 21;   // 3D fields of at least this many voxels that the planar
+                                             // kernel takes get its own launches (a graph branch)
 };
 
 static int batch_run(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, cudaStream_t s, const BatchPlan &plan);
@@ -566,12 +569,18 @@ static int batch_run(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, cudaSt
     std::vector<BField> bf;
     std::vector<BItem> items;
     std::vector<int> separate;   // 3D fields with more levels than 16-bit comparison lanes hold, or 6-connected
+    std::vector<int> planar;     // large 3D fields the planar kernel takes: own launches, a graph branch
     size_t hist_entries = 0, max_smem_entries = 0;
     for (int oi = 0; oi < n; oi++) {
         const ec_field_desc &d = fields[order[oi]];
         if (d.L == 0) continue;
         if (d.ndim == 3 && (d.L > kMaxFastL3 || d.connectivity == 6)) {
             separate.push_back(order[oi]);
+            continue;
+        }
+        if (d.ndim == 3 && vox(order[oi]) >= plan.planar_min &&
+            planar_3d_supported(d.field, d.dims, d.dtype, d.thresholds, d.L, d.descriptors)) {
+            planar.push_back(order[oi]);
             continue;
         }
         BField F{};
@@ -648,7 +657,28 @@ static int batch_run(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, cudaSt
                            ctx->ws, s);
         if (rc) return rc;
     }
-    if (bf.empty()) return EC_OK;
+    // the planar fields' launch sequences (scratch sized first: none is
+    // allocated while a graph is captured)
+    size_t planar_scratch = 0;
+    for (int i : planar)
+        planar_scratch = std::max(planar_scratch, curve_scratch_bytes(fields[i].descriptors, fields[i].L));
+    if (!planar.empty()) {
+        const int rc = ensure_scratch(ctx, planar_scratch);
+        if (rc) return rc;
+    }
+    auto enqueue_planar = [&](cudaStream_t st) -> int {
+        for (int i : planar) {
+            const ec_field_desc &d = fields[i];
+            CurvePlan cp;
+            cp.algo = ALGO_PLANAR;
+            cp.num_sms = ctx->num_sms;
+            const int rc = enqueue_curve(cp, 3, d.field, d.dims, d.dtype, d.thresholds, d.L, d.connectivity,
+                                         d.descriptors, d.out, ctx->ws, st);
+            if (rc) return rc;
+        }
+        return EC_OK;
+    };
+    if (bf.empty()) return enqueue_planar(s);
     if (items.size() > (size_t)INT32_MAX) { set_error("batch too large"); return EC_ERR_UNSUPPORTED; }
 
     // ---- device layout: [flags 256][fields][items][counters][hist]
@@ -675,6 +705,8 @@ static int batch_run(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, cudaSt
         st.staging_bytes = want;
     }
     if (!st.staged_free) EC_CUDA(cudaEventCreateWithFlags(&st.staged_free, cudaEventDisableTiming));
+    if (!st.fork) EC_CUDA(cudaEventCreateWithFlags(&st.fork, cudaEventDisableTiming));
+    if (!st.join) EC_CUDA(cudaEventCreateWithFlags(&st.join, cudaEventDisableTiming));
     char *base = (char *)st.dev;
     int *flags = (int *)base;
     BField *d_fields = (BField *)(base + 256);
@@ -696,18 +728,34 @@ static int batch_run(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, cudaSt
     grid = std::min<int>(grid, (int)items.size());
 
     // ---- capture the sequence into a graph; update the cached executable if possible
-    cudaStream_t cap = nullptr;
+    // the planar fields run on a second branch of the same graph, beside
+    // the persistent kernel
+    cudaStream_t cap = nullptr, cap2 = nullptr;
     EC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    if (!planar.empty() && cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamDestroy(cap);
+        return cuda_fail(cudaGetLastError(), "batch stream creation");
+    }
     cudaGraph_t graph = nullptr;
+    int prc = EC_OK;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
+        if (cap2) {
+            cudaEventRecord(st.fork, cap);
+            cudaStreamWaitEvent(cap2, st.fork, 0);
+            prc = enqueue_planar(cap2);
+            cudaEventRecord(st.join, cap2);
+        }
         cudaMemcpyAsync(d_fields, st.staging, table_bytes, cudaMemcpyHostToDevice, cap);
         cudaMemsetAsync(flags, 0, 256, cap);
         cudaMemsetAsync(d_counters, 0, ct_bytes + hs_bytes, cap);
         k_batch<<<grid, kThreads, smem, cap>>>(d_fields, d_items, (int)items.size(), d_counters, flags, hist_cap);
+        if (cap2) cudaStreamWaitEvent(cap, st.join, 0);
         e = cudaStreamEndCapture(cap, &graph);
     }
     cudaStreamDestroy(cap);
+    if (cap2) cudaStreamDestroy(cap2);
+    if (prc) { if (graph) cudaGraphDestroy(graph); return prc; }
     if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e, "batch graph capture"); }
     bool updated = false;
     if (st.exec) {
@@ -738,6 +786,8 @@ void ec::batch_release(ec_ctx *ctx)
     if (!st) return;
     if (st->exec) cudaGraphExecDestroy(st->exec);
     if (st->staged_free) cudaEventDestroy(st->staged_free);
+    if (st->fork) cudaEventDestroy(st->fork);
+    if (st->join) cudaEventDestroy(st->join);
     if (st->dev) cudaFree(st->dev);
     if (st->staging) cudaFreeHost(st->staging);
     delete st;

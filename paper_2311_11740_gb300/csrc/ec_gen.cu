@@ -2,18 +2,21 @@
 // low-memory (streaming) workload.  This is input generation, not part of
 // the EC computation.
 //
-//   h(x,y,z) = low 16 bits of SplitMix64(seed*2^48 ^ (z mod 2^16)*2^32
-//                                        ^ (y mod 2^16)*2^16 ^ (x mod 2^16))
+//   m(u)     = MurmurHash3's 32-bit finaliser (Appleby): u ^= u >> 16;
+//              u *= 0x85EBCA6B; u ^= u >> 13; u *= 0xC2B2AE35; u ^= u >> 16
+//   a        = m(lo32(seed) ^ m(hi32(seed)))
+//   h(x,y,z) = low 16 bits of m(m(m(a ^ z) ^ y) ^ x)    (x, y, z mod 2^32)
 //   v(x,y,z) = floor( sum over the 5x5x5 box around (x,y,z) of h / 2000 )
-// (4096 / (125 * 65536) = 1 / 2000, so v lies in [0, 4095]).  SplitMix64 is
-// Steele, Lea and Flood's published finaliser (OOPSLA 2014).  The field is
+// (4096 / (125 * 65536) = 1 / 2000, so v lies in [0, 4095]).  The field is
 // defined for every integer coordinate, so any sub-box can be generated.
 //
 // One block produces a 64 x 32 column of outputs and walks it along z.  Per
 // input plane: the 68 x 36 hashes of its neighbourhood go to shared memory
-// (1.2 hashes per output), 5-wide sums along x are formed four at a time as
-// running sums, and each thread sums 5 rows of those for its 4 x 2 outputs
-// and keeps the last five such plane sums in registers for the sum along z.
+// (1.2 hashes per output; the per-row keys m(m(a ^ z) ^ y) are formed one
+// plane ahead by 36 threads), 5-wide sums along x are formed four at a time
+// as running sums, each thread sums 5 rows of those for its 4 x 2 outputs,
+// and a running sum over the last five planes (a register ring indexed at
+// compile time: the plane loop is unrolled by five) gives the sum along z.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,83 +25,142 @@
 namespace {
 
 constexpr int GX = 64, GY = 32, HX = GX + 4, HY = GY + 4;
+constexpr int SEG = 10, NSEG = 7, HXP = 72;   // hash row segments per thread; padded hash row (>= SEG * NSEG)
 
-__device__ __forceinline__ uint32_t hash16(uint64_t seed, int64_t x, int64_t y, int64_t z)
+__host__ __device__ __forceinline__ uint32_t fmix32(uint32_t u)
 {
-    uint64_t v = (seed << 48) ^ (((uint64_t)z & 0xFFFFull) << 32) ^ (((uint64_t)y & 0xFFFFull) << 16) ^
-                 ((uint64_t)x & 0xFFFFull);
-    v += 0x9E3779B97F4A7C15ull;
-    v = (v ^ (v >> 30)) * 0xBF58476D1CE4E5B9ull;
-    v = (v ^ (v >> 27)) * 0x94D049BB133111EBull;
-    v ^= v >> 31;
-    return (uint32_t)(v & 0xFFFFull);
+    u ^= u >> 16;
+    u *= 0x85EBCA6Bu;
+    u ^= u >> 13;
+    u *= 0xC2B2AE35u;
+    u ^= u >> 16;
+    return u;
 }
 
-__global__ void __launch_bounds__(256) k_hashbox(uint64_t seed, int64_t ox, int64_t oy, int64_t oz, int64_t nx,
+struct GenCtx {
+    uint32_t a;
+    int64_t ox, oy, oz, nx, ny, nz, bx0, by0;
+    int tx, ty;
+    int hrow, hseg;          // this thread's hash row and 10-wide segment (hrow >= HY: none)
+    uint16_t *out[2];        // output rows 2ty, 2ty+1 of plane 0 at x = bx0 + 4tx (nullptr: past the box)
+    int64_t plane;           // elements per output plane
+    bool vec;                // four outputs as one 8-byte store
+};
+
+// Row keys of input plane k (relative to oz) into rk: threads 0..HY-1.
+__device__ __forceinline__ void row_keys(const GenCtx &g, int64_t k, uint32_t *rk)
+{
+    if (threadIdx.x < HY) {
+        const uint32_t pk = fmix32(g.a ^ (uint32_t)(g.oz + k));
+        rk[threadIdx.x] = fmix32(pk ^ (uint32_t)(g.oy + g.by0 - 2 + (int64_t)threadIdx.x));
+    }
+}
+
+// One input plane k: hashes, sums along x and y, the running sum along z
+// (ring slot J holds this plane's sums until five planes later), and the
+// output plane k - 2 once its five-plane window is complete.
+template <int J>
+__device__ __forceinline__ void gen_plane(const GenCtx &g, int64_t k, uint32_t (*hs)[HXP], uint32_t (*xs)[GX],
+                                          uint32_t (*rk)[HY], uint32_t (&ring)[5][8], uint32_t (&zs)[8])
+{
+    if (g.hrow < HY) {
+        // ten consecutive hashes of one row (the padding columns 68..71 are never read)
+        const uint32_t key = rk[k & 1][g.hrow];
+        const uint32_t x0 = (uint32_t)(g.ox + g.bx0 - 2) + (uint32_t)(SEG * g.hseg);
+        uint32_t *row = &hs[g.hrow][SEG * g.hseg];
+#pragma unroll
+        for (int j = 0; j < SEG; j++) row[j] = fmix32(key ^ (x0 + (uint32_t)j)) & 0xFFFFu;
+    }
+    __syncthreads();
+    row_keys(g, k + 1, rk[(k + 1) & 1]);   // next plane's keys (read after the next barrier)
+    for (int i = threadIdx.x; i < HY * (GX / 4); i += blockDim.x) {
+        const int ly = i >> 4, q = i & 15;
+        const uint4 a = *(const uint4 *)&hs[ly][4 * q], b = *(const uint4 *)&hs[ly][4 * q + 4];
+        uint4 o;
+        o.x = a.x + a.y + a.z + a.w + b.x;
+        o.y = o.x - a.x + b.y;
+        o.z = o.y - a.y + b.z;
+        o.w = o.z - a.z + b.w;
+        *(uint4 *)&xs[ly][4 * q] = o;
+    }
+    __syncthreads();
+    uint4 r[6];
+#pragma unroll
+    for (int j = 0; j < 6; j++) r[j] = *(const uint4 *)&xs[2 * g.ty + j][4 * g.tx];
+    uint32_t s[8];
+    s[0] = r[0].x + r[1].x + r[2].x + r[3].x + r[4].x;
+    s[1] = r[0].y + r[1].y + r[2].y + r[3].y + r[4].y;
+    s[2] = r[0].z + r[1].z + r[2].z + r[3].z + r[4].z;
+    s[3] = r[0].w + r[1].w + r[2].w + r[3].w + r[4].w;
+    s[4] = s[0] - r[0].x + r[5].x;
+    s[5] = s[1] - r[0].y + r[5].y;
+    s[6] = s[2] - r[0].z + r[5].z;
+    s[7] = s[3] - r[0].w + r[5].w;
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        zs[b] += s[b] - ring[J][b];   // the plane five back leaves the window
+        ring[J][b] = s[b];
+    }
+    const int64_t zo = k - 2;   // output plane whose 5-plane window just completed
+    if (zo < 0) return;
+    const int64_t x = g.bx0 + 4 * g.tx;
+#pragma unroll
+    for (int yy = 0; yy < 2; yy++) {
+        if (!g.out[yy]) continue;
+        uint32_t v[4];
+#pragma unroll
+        for (int b = 0; b < 4; b++) v[b] = zs[4 * yy + b] / 2000u;
+        uint16_t *o = g.out[yy] + zo * g.plane;
+        if (g.vec) {
+            *(uint2 *)o = make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; b++)
+                if (x + b < g.nx) o[b] = (uint16_t)v[b];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 3) k_hashbox(uint64_t seed, int64_t ox, int64_t oy, int64_t oz, int64_t nx,
                                                  int64_t ny, int64_t nz, uint16_t *__restrict__ dst)
 {
-    __shared__ __align__(16) uint32_t hs[HY][HX];   // hashes of the plane's neighbourhood
+    __shared__ __align__(16) uint32_t hs[HY][HXP];  // hashes of the plane's neighbourhood
     __shared__ __align__(16) uint32_t xs[HY][GX];   // 5-wide sums along x
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // outputs x 4tx .. 4tx+3, y 2ty, 2ty+1
-    const int64_t bx0 = (int64_t)blockIdx.x * GX, by0 = (int64_t)blockIdx.y * GY;
-    uint32_t ring[5][8];
+    __shared__ uint32_t rk[2][HY];                  // row keys of this plane and the next
+    GenCtx g;
+    g.a = fmix32((uint32_t)seed ^ fmix32((uint32_t)(seed >> 32)));
+    g.ox = ox; g.oy = oy; g.oz = oz; g.nx = nx; g.ny = ny; g.nz = nz;
+    g.bx0 = (int64_t)blockIdx.x * GX;
+    g.by0 = (int64_t)blockIdx.y * GY;
+    g.tx = threadIdx.x & 15;   // outputs x 4tx .. 4tx+3
+    g.ty = threadIdx.x >> 4;   // outputs y 2ty, 2ty+1
+    g.hrow = threadIdx.x / NSEG;
+    g.hseg = threadIdx.x - g.hrow * NSEG;
+    g.plane = ny * nx;
+    const int64_t x = g.bx0 + 4 * g.tx;
+    for (int yy = 0; yy < 2; yy++) {
+        const int64_t y = g.by0 + 2 * g.ty + yy;
+        g.out[yy] = (y < ny && x < nx) ? dst + y * nx + x : nullptr;
+    }
+    // rows, planes and x all keep 8-byte alignment when nx is a multiple of 4
+    g.vec = x + 3 < nx && (nx & 3) == 0 && ((uintptr_t)dst & 7u) == 0;
+    uint32_t ring[5][8], zs[8];
 #pragma unroll
-    for (int a = 0; a < 5; a++)
+    for (int b = 0; b < 8; b++) {
+        zs[b] = 0;
 #pragma unroll
-        for (int b = 0; b < 8; b++) ring[a][b] = 0;
-    for (int64_t k = -2; k < nz + 2; k++) {
-        const int64_t z = oz + k;
-        for (int i = threadIdx.x; i < HX * HY; i += blockDim.x) {
-            const int ly = i / HX, lx = i - ly * HX;
-            hs[ly][lx] = hash16(seed, ox + bx0 - 2 + lx, oy + by0 - 2 + ly, z);
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < HY * (GX / 4); i += blockDim.x) {
-            const int ly = i >> 4, q = i & 15;
-            const uint4 a = *(const uint4 *)&hs[ly][4 * q], b = *(const uint4 *)&hs[ly][4 * q + 4];
-            uint4 o;
-            o.x = a.x + a.y + a.z + a.w + b.x;
-            o.y = o.x - a.x + b.y;
-            o.z = o.y - a.y + b.z;
-            o.w = o.z - a.z + b.w;
-            *(uint4 *)&xs[ly][4 * q] = o;
-        }
-        __syncthreads();
-        uint4 r[6];
-#pragma unroll
-        for (int j = 0; j < 6; j++) r[j] = *(const uint4 *)&xs[2 * ty + j][4 * tx];
-        uint32_t s[8];
-        s[0] = r[0].x + r[1].x + r[2].x + r[3].x + r[4].x;
-        s[1] = r[0].y + r[1].y + r[2].y + r[3].y + r[4].y;
-        s[2] = r[0].z + r[1].z + r[2].z + r[3].z + r[4].z;
-        s[3] = r[0].w + r[1].w + r[2].w + r[3].w + r[4].w;
-        s[4] = s[0] - r[0].x + r[5].x;
-        s[5] = s[1] - r[0].y + r[5].y;
-        s[6] = s[2] - r[0].z + r[5].z;
-        s[7] = s[3] - r[0].w + r[5].w;
-#pragma unroll
-        for (int b = 0; b < 8; b++) {
-            ring[0][b] = ring[1][b]; ring[1][b] = ring[2][b]; ring[2][b] = ring[3][b]; ring[3][b] = ring[4][b];
-            ring[4][b] = s[b];
-        }
-        const int64_t zo = k - 2;   // output plane whose 5-plane window just completed
-        if (zo >= 0) {
-#pragma unroll
-            for (int yy = 0; yy < 2; yy++) {
-                const int64_t y = by0 + 2 * ty + yy, x = bx0 + 4 * tx;
-                if (y >= ny) continue;
-                uint16_t v[4];
-#pragma unroll
-                for (int b = 0; b < 4; b++) {
-                    const int e = 4 * yy + b;
-                    v[b] = (uint16_t)((ring[0][e] + ring[1][e] + ring[2][e] + ring[3][e] + ring[4][e]) / 2000u);
-                }
-                uint16_t *row = dst + (zo * ny + y) * nx;
-#pragma unroll
-                for (int b = 0; b < 4; b++)
-                    if (x + b < nx) row[x + b] = v[b];
-            }
-        }
+        for (int a = 0; a < 5; a++) ring[a][b] = 0;
+    }
+    row_keys(g, -2, rk[(-2) & 1]);
+    __syncthreads();
+    // input planes -2 .. nz+1; ring slot = (k + 2) mod 5
+    const int64_t kend = nz + 2;
+    for (int64_t k = -2; k < kend; k += 5) {
+        gen_plane<0>(g, k, hs, xs, rk, ring, zs);
+        if (k + 1 < kend) gen_plane<1>(g, k + 1, hs, xs, rk, ring, zs);
+        if (k + 2 < kend) gen_plane<2>(g, k + 2, hs, xs, rk, ring, zs);
+        if (k + 3 < kend) gen_plane<3>(g, k + 3, hs, xs, rk, ring, zs);
+        if (k + 4 < kend) gen_plane<4>(g, k + 4, hs, xs, rk, ring, zs);
     }
 }
 

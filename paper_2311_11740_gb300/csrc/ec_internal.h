@@ -72,9 +72,14 @@ int launch_curve_2d(const void *field, const int64_t dims[2], const BinArgs &ba,
 // as never active (slab halos at the field's ends).
 int launch_fast_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha, int tile_z,
                    int grid_override, int num_sms, int *err_flag, cudaStream_t s, const int zrange[4] = nullptr);
-// The planar-form kernel for float32 fields staged by TMA (at most 1024
-// levels; descriptor sets EC, EC|AREA|VOLUME, all four); EC_ERR_UNSUPPORTED
-// without launching for anything else.
+// Does the planar kernel take this 3D request (dtype, levels, descriptor
+// set, row alignment for the tensor map)?
+bool planar_3d_supported(const void *field, const int64_t dims[3], int dtype, const void *thr, int32_t L,
+                         uint32_t desc);
+// The planar-form kernel for fields staged by TMA (float32 with at most 1024
+// levels and descriptor sets EC, EC|AREA|VOLUME or all four; uint16 with
+// identity levels, EC or EC|VOLUME); EC_ERR_UNSUPPORTED without launching
+// for anything else.
 int launch_planar_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha, int tile_z,
                      int grid_override, int num_sms, int *err_flag, cudaStream_t s, const int zrange[4] = nullptr);
 // cuTensorMapEncodeTiled from the driver (nullptr if unavailable).

@@ -522,6 +522,19 @@ static int launch_dm(const CUtensorMap &map, Params p, int tile_z, int num_sms, 
 // the descriptor sets EC, EC|AREA|VOLUME or all four; uint16 with identity
 // levels, at most 4096 levels and EC or EC|VOLUME.  Returns
 // EC_ERR_UNSUPPORTED (without launching) for anything else.
+bool planar_3d_supported(const void *field, const int64_t dims[3], int dtype, const void *thr, int32_t L,
+                         uint32_t desc)
+{
+    using namespace planar3d;
+    const bool f32 = dtype == EC_F32 && thr && L >= 1 && L <= LCAP<float>() &&
+                     (desc == 1u || desc == 13u || desc == 15u);
+    const bool u16 = dtype == EC_U16 && !thr && L >= 1 && L <= LCAP<uint16_t>() && (desc == 1u || desc == 9u);
+    if (!f32 && !u16) return false;
+    const int esz = f32 ? 4 : 2;
+    return (dims[2] * esz) % 16 == 0 && ((uintptr_t)field % 16) == 0 && dims[0] <= INT32_MAX / 2 &&
+           dims[1] <= INT32_MAX / 2 && dims[2] <= INT32_MAX / 2;
+}
+
 int launch_planar_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha, int tile_z,
                      int grid_override, int num_sms, int *err_flag, cudaStream_t s, const int zrange[4])
 {
@@ -529,15 +542,9 @@ int launch_planar_3d(const void *field, const int64_t dims[3], const BinArgs &ba
     uint32_t desc = 0;
     for (int i = 0; i < kMaxDesc; i++)
         if (ha.rows.row[i] >= 0) desc |= 1u << i;
-    const bool f32 = ba.dtype == EC_F32 && ba.thr && ba.L >= 1 && ba.L <= LCAP<float>() &&
-                     (desc == 1u || desc == 13u || desc == 15u);
-    const bool u16 = ba.dtype == EC_U16 && !ba.thr && ba.L >= 1 && ba.L <= LCAP<uint16_t>() &&
-                     (desc == 1u || desc == 9u);
-    if (!f32 && !u16) return EC_ERR_UNSUPPORTED;
+    if (!planar_3d_supported(field, dims, ba.dtype, ba.thr, ba.L, desc)) return EC_ERR_UNSUPPORTED;
+    const bool f32 = ba.dtype == EC_F32;
     const int esz = f32 ? 4 : 2;
-    if ((dims[2] * esz) % 16 != 0 || ((uintptr_t)field % 16) != 0 || dims[0] > INT32_MAX / 2 ||
-        dims[1] > INT32_MAX / 2 || dims[2] > INT32_MAX / 2)
-        return EC_ERR_UNSUPPORTED;
     PFN_cuTensorMapEncodeTiled_v12000 enc = (PFN_cuTensorMapEncodeTiled_v12000)tma_encode_fn();
     if (!enc) return EC_ERR_UNSUPPORTED;
     Params p{};

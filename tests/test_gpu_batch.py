@@ -138,3 +138,25 @@ def test_batch_rejects_bad_field(ctx):
     with pytest.raises(ec.ECError) as e:
         ec.batch([dict(field=f, thresholds=t, connectivity=8)], ctx=ctx)
     assert e.value.status == 1
+
+
+def test_batch_planar_branch_fields(ctx):
+    """Large 3D fields the planar kernel takes run as their own launches on a
+    second branch of the batch's graph, beside the persistent kernel for the
+    rest; every field still gets the oracle's curves, on repeated calls and
+    with the branch's field count changing."""
+    f1, t1 = workloads.config3(n=132, nblobs=40, L=700)
+    f2, t2 = workloads.config3(n=136, nblobs=30, L=1024)
+    u = np.clip(workloads.grf_nd(5, (128, 136, 136), 3.0).numpy() * 300 + 300, 0, 599).astype(np.uint16)
+    big = [
+        dict(field=f1.numpy(), thr=t1.numpy(), L=700, conn=26, desc=13),
+        dict(field=f2.numpy()[:, :, :132].copy(), thr=t2.numpy(), L=1024, conn=26, desc=15),
+        dict(field=f1.numpy(), thr=t1.numpy(), L=700, conn=26, desc=1),
+        dict(field=u, thr=None, L=600, conn=26, desc=9),
+        dict(field=f2.numpy()[:, :, :130].copy(), thr=t2.numpy(), L=1024, conn=26, desc=13),   # rows not 16 B
+    ]
+    small = _mixed_fields(31, 10)
+    for fields in (big + small, big[:2] + small, small + big):
+        got, _ = _run_batch(ctx, fields)
+        for f, g in zip(fields, got):
+            np.testing.assert_array_equal(g, oracle.ec_curves(f["field"], f["thr"], f["L"], f["conn"], f["desc"]))

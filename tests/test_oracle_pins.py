@@ -372,22 +372,24 @@ def test_binning_matches_searchsorted_semantics():
 
 # ------------------------------------------------------------ hash-box field
 
-def _splitmix64(z):
-    M = (1 << 64) - 1
-    z = (z + 0x9E3779B97F4A7C15) & M
-    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
-    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
-    return z ^ (z >> 31)
+def _fmix32(u):
+    u ^= u >> 16
+    u = (u * 0x85EBCA6B) & 0xFFFFFFFF
+    u ^= u >> 13
+    u = (u * 0xC2B2AE35) & 0xFFFFFFFF
+    return u ^ (u >> 16)
 
 
 def test_hashbox_matches_definition():
-    seed = 4
+    seed = (7 << 32) | 4
+    a = _fmix32((seed & 0xFFFFFFFF) ^ _fmix32(seed >> 32))
     got = oracle.hashbox_u16(seed, -3, 5, 2046, 4, 3, 2)
     for k, j, i in itertools.product(range(2), range(3), range(4)):
         x, y, z = -3 + i, 5 + j, 2046 + k
         s = 0
         for dz, dy, dx in itertools.product(range(-2, 3), repeat=3):
-            ctr = (seed << 48) ^ (((z + dz) & 0xFFFF) << 32) ^ (((y + dy) & 0xFFFF) << 16) ^ ((x + dx) & 0xFFFF)
-            s += _splitmix64(ctr) & 0xFFFF
+            hz = _fmix32(a ^ ((z + dz) & 0xFFFFFFFF))
+            hy = _fmix32(hz ^ ((y + dy) & 0xFFFFFFFF))
+            s += _fmix32(hy ^ ((x + dx) & 0xFFFFFFFF)) & 0xFFFF
         assert got[k, j, i] == (s * 4096) // (125 * 65536)
     assert got.max() < 4096
