@@ -66,8 +66,15 @@ template <typename T>
 constexpr int XOFF() { return 16 / (int)sizeof(T); }
 template <typename T>
 constexpr int BXT() { return TX + 2 * XOFF<T>(); }
-template <typename T>
-constexpr int SLOT_BYTES() { return (BXT<T>() * BY * (int)sizeof(T) + 127) / 128 * 128; }
+// Row-copy staging (float32 rows that are not a multiple of 16 bytes, which
+// a tensor map cannot describe): each staged row is one 16-byte aligned
+// bulk copy of RPITCH floats starting at or up to 3 floats before x0 - 4.
+constexpr int RPITCH = BXT<float>() + 4;
+template <typename T, bool RW = false>
+constexpr int SLOT_BYTES()
+{
+    return RW ? (RPITCH * BY * 4 + 127) / 128 * 128 : (BXT<T>() * BY * (int)sizeof(T) + 127) / 128 * 128;
+}
 // Levels the shared histograms hold.
 template <typename T>
 constexpr int LCAP() { return sizeof(T) == 4 ? 1024 : 4096; }
@@ -75,12 +82,12 @@ template <typename T>
 constexpr int HW() { return LCAP<T>() + 1; }   // words per histogram row (level L = never active)
 
 // shared-memory layout (bytes)
-template <typename T>
-constexpr size_t OFF_KEYS() { return (size_t)NS * SLOT_BYTES<T>(); }
-template <typename T>
-constexpr size_t OFF_BARS() { return OFF_KEYS<T>() + (size_t)NK * KWORDS * 4; }
-template <typename T>
-constexpr size_t OFF_HIST() { return OFF_BARS<T>() + NS * 8 + 16; }
+template <typename T, bool RW = false>
+constexpr size_t OFF_KEYS() { return (size_t)NS * SLOT_BYTES<T, RW>(); }
+template <typename T, bool RW = false>
+constexpr size_t OFF_BARS() { return OFF_KEYS<T, RW>() + (size_t)NK * KWORDS * 4; }
+template <typename T, bool RW = false>
+constexpr size_t OFF_HIST() { return OFF_BARS<T, RW>() + NS * 8 + 16; }
 // Histogram rows per descriptor set:
 //   EC (1):                  EC
 //   EC | VOLUME (9):         EC, volume (one +1 atomic per voxel)
@@ -91,10 +98,10 @@ constexpr int hist_rows() { return DM == 1 ? 1 : (DM == 9 ? 2 : (DM == 13 ? 4 : 
 template <int DM>
 constexpr int R_VOL() { return DM == 9 ? 1 : 3; }
 enum { R_EC = 0, R_PACK = 1, R_AREA = 2, R_PER = 4 };
-template <typename T, int DM>
-constexpr size_t off_thr() { return OFF_HIST<T>() + (((size_t)hist_rows<DM>() * HW<T>() * 4 + 15) & ~(size_t)15); }
-template <typename T, int DM>
-constexpr size_t smem_bytes() { return off_thr<T, DM>() + (sizeof(T) == 4 ? (size_t)LCAP<T>() * 4 : 0); }
+template <typename T, int DM, bool RW = false>
+constexpr size_t off_thr() { return OFF_HIST<T, RW>() + (((size_t)hist_rows<DM>() * HW<T>() * 4 + 15) & ~(size_t)15); }
+template <typename T, int DM, bool RW = false>
+constexpr size_t smem_bytes() { return off_thr<T, DM, RW>() + (sizeof(T) == 4 ? (size_t)LCAP<T>() * 4 : 0); }
 
 struct Params {
     int64_t D, H, W;
@@ -108,6 +115,8 @@ struct Params {
     int *err;              // bit 2: a bounded wait gave up
     const int *uni;        // [0] = 1 if the uniform-spacing guess is exact, [1], [2] = its scale and offset
     int test_give_up;      // testing: give up the first bounded wait of every block
+    const float *field;    // row-copy staging: the field (16-byte aligned start) and its element count
+    int64_t nelem;
 };
 
 struct Ctx {
@@ -121,7 +130,14 @@ struct Ctx {
     uint32_t left0, left1;     // leftover binning pairs: row | pair << 16 | plane << 31, or ~0
     int x0, y0, z0, z1, zv0, zv1;
     int64_t H, W;
-    bool edge;                 // uint16 fields: the item's staged box reaches outside the field
+    bool edge;                 // the item's staged box reaches outside the field (uint16 and row-copy
+                               // staging test coordinates; float32 tensor-map staging reads NaN there)
+    const float *field;        // row-copy staging
+    int64_t nelem;
+    int64_t HW;                // H * W
+    int hw4, w4;               // H * W and W mod 4 (a staged row's start phase)
+    int Hi, Wi;                // H, W as 32-bit values
+    uint32_t emask;            // out_mask bits of this thread's four fixed key pairs on edge items
     uint32_t base;             // ring sequence number of plane z0 - 1
     uint32_t parity;
     uint32_t inflight;         // thread 0: ring slots with a TMA copy issued and not yet waited for
@@ -151,12 +167,22 @@ __device__ __forceinline__ uint32_t left_share(int j)
     return (uint32_t)row | ((uint32_t)pair << 16) | (plane << 31);
 }
 
+// Cells of key pair (row, pair) outside the field: bit 0 for the pair's
+// first cell, bit 1 for its second (coordinates fit in 32 bits).
+__device__ __forceinline__ uint32_t out_mask(const Ctx &c, int row, int pair)
+{
+    const int gy = c.y0 - 1 + row, gx = c.x0 - 2 + 2 * pair;
+    const bool yin = gy >= 0 && gy < c.Hi;
+    return ((yin && gx >= 0 && gx < c.Wi) ? 0u : 1u) | ((yin && gx + 1 >= 0 && gx + 1 < c.Wi) ? 0u : 2u);
+}
+
 // Key pair (row, pair p) of a staged plane.  float32: the spacing guess with
-// one threshold read (UNI) or the general search.  uint16 with identity
-// levels: min(v, L) per lane; on edge items a lane whose cell lies outside
-// the field reads L (out-of-bounds TMA elements are 0).
+// one threshold read (UNI) or the general search (cells outside the field
+// were staged as NaN and bin to L).  uint16 with identity levels: min(v, L)
+// per lane; cells outside the field (om, see out_mask) read L (the tensor
+// map stages them as 0).
 template <typename T, bool UNI>
-__device__ __forceinline__ void bin_pair2(const Ctx &c, uint32_t *kp, const T *fp, int row, int pair)
+__device__ __forceinline__ void bin_pair2(const Ctx &c, uint32_t *kp, const T *fp, uint32_t om)
 {
     if constexpr (sizeof(T) == 4) {
         const float2 v = *(const float2 *)fp;
@@ -166,14 +192,89 @@ __device__ __forceinline__ void bin_pair2(const Ctx &c, uint32_t *kp, const T *f
     } else {
         const uint32_t L = (uint32_t)c.fb.L;
         uint32_t k = vmin2(*(const uint32_t *)fp, L | (L << 16));
-        if (c.edge) {
-            const int64_t gy = (int64_t)c.y0 - 1 + row, gx = (int64_t)c.x0 - 2 + 2 * pair;
-            const bool yin = gy >= 0 && gy < c.H;
-            if (!(yin && gx >= 0 && gx < c.W)) k = (k & 0xFFFF0000u) | L;
-            if (!(yin && gx + 1 >= 0 && gx + 1 < c.W)) k = (k & 0x0000FFFFu) | (L << 16);
-        }
+        if (om & 1u) k = (k & 0xFFFF0000u) | L;
+        if (om & 2u) k = (k & 0x0000FFFFu) | (L << 16);
         *kp = k;
     }
+}
+
+// Row-copy staging: key pair p of a staged row whose element x0 - 4 sits r
+// floats into the row (the copy starts at the 16-byte boundary at or below
+// it); cells outside the field (om) read L.
+template <bool UNI>
+__device__ __forceinline__ void bin_pair_rw(const Ctx &c, uint32_t *kp, const float *srow, int pair, uint32_t om)
+{
+    const float *fp = srow + 2 + 2 * pair;
+    const float v0 = fp[0], v1 = fp[1];
+    const uint32_t L = (uint32_t)c.fb.L;
+    uint32_t b0 = UNI ? fast3d::fbin_uniform(v0, c.fb) : fast3d::fbin(v0, c.fb);
+    uint32_t b1 = UNI ? fast3d::fbin_uniform(v1, c.fb) : fast3d::fbin(v1, c.fb);
+    if (om & 1u) b0 = L;
+    if (om & 2u) b1 = L;
+    *kp = b0 | (b1 << 16);
+}
+
+// Staged row `row` of a row-copy slot, from its element x0 - 4 on: rb is
+// the start phase of row 0 ((plane * H + y0 - 1) * W + x0 mod 4).
+__device__ __forceinline__ const float *rw_row(const Ctx &c, const float *slot, uint32_t rb, int row)
+{
+    return slot + row * RPITCH + (int)((rb + (uint32_t)(row * c.w4)) & 3u);
+}
+
+template <bool UNI>
+__device__ __forceinline__ void bin_plane_rw(const Ctx &c, uint32_t *kp, const float *slot, int plane, uint32_t q)
+{
+    const int ko = c.tr * KP + c.tc;
+    const uint32_t rb = (uint32_t)plane * (uint32_t)c.hw4 + (uint32_t)((c.y0 - 1) * c.w4 + c.x0);
+    const float *r0 = rw_row(c, slot, rb, c.tr), *r1 = rw_row(c, slot, rb, c.tr + 16);
+    bin_pair_rw<UNI>(c, kp + ko, r0, c.tc, c.emask & 3u);
+    bin_pair_rw<UNI>(c, kp + ko + 16, r0, c.tc + 16, (c.emask >> 2) & 3u);
+    bin_pair_rw<UNI>(c, kp + ko + 16 * KP, r1, c.tc, (c.emask >> 4) & 3u);
+    bin_pair_rw<UNI>(c, kp + ko + 16 * KP + 16, r1, c.tc + 16, (c.emask >> 6) & 3u);
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+        const uint32_t lv = e ? c.left1 : c.left0;
+        if (lv != ~0u && (lv >> 31) == q) {
+            const int row = (int)(lv & 0xFFFFu), pair = (int)((lv >> 16) & 0x7FFFu);
+            bin_pair_rw<UNI>(c, kp + row * KP + pair, rw_row(c, slot, rb, row), pair,
+                             c.edge ? out_mask(c, row, pair) : 0u);
+        }
+    }
+}
+
+// Row-copy staging of plane `plane` (every thread): the 34 staged rows are
+// 19 16-byte chunks each, from the 16-byte boundary at or below element
+// x0 - 4 of the row (646 chunks, thread t takes chunks t, t + 256, t + 512).
+// A chunk is one cp.async; the part of a chunk outside the field's memory is
+// zero-filled (those positions lie outside the field and are binned to L).
+// Rows and planes outside the field are not read.  Each thread then makes
+// the slot's barrier (expecting one arrival per thread) track its copies.
+__device__ __forceinline__ void issue_plane_rw(Ctx &c, int plane)
+{
+    constexpr int CPR = RPITCH / 4;   // chunks per row
+    const uint32_t s = slot_of(c, plane);
+    unsigned char *slot = c.ring + (size_t)s * SLOT_BYTES<float, true>();
+    if (plane >= c.zv0 && plane < c.zv1) {
+        const int64_t pb = (int64_t)plane * c.HW + (c.x0 - 4);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const int q = threadIdx.x + k * kThreads;
+            if (q < BY * CPR) {
+                const int row = q / CPR, ch = q - row * CPR;
+                const int gy = c.y0 - 1 + row;
+                if (gy >= 0 && gy < c.H) {
+                    const int64_t src = ((pb + (int64_t)gy * (int)c.W) & ~(int64_t)3) + 4 * ch;
+                    const int64_t left = c.nelem - src;
+                    const uint32_t bytes = src < 0 ? 0u : (left >= 4 ? 16u : (uint32_t)(left > 0 ? left * 4 : 0));
+                    const float *g = bytes ? c.field + src : c.field;
+                    fast3d::cp_async16(fast3d::smem_u32(slot + (size_t)row * RPITCH * 4 + ch * 16), g, bytes);
+                }
+            }
+        }
+    }
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(fast3d::smem_u32(&c.bars[s]))
+                 : "memory");
+    if (threadIdx.x == 0) c.inflight |= 1u << s;
 }
 
 // Bin one staged plane (q = 0: the first of the barrier step, 1: the second):
@@ -183,16 +284,17 @@ __device__ __forceinline__ void bin_plane(const Ctx &c, uint32_t *kp, const T *f
 {
     constexpr int BX = BXT<T>(), F0 = XOFF<T>() - 2;
     const int fo = c.tr * BX + F0 + 2 * c.tc, ko = c.tr * KP + c.tc;
-    bin_pair2<T, UNI>(c, kp + ko, fp + fo, c.tr, c.tc);
-    bin_pair2<T, UNI>(c, kp + ko + 16, fp + fo + 32, c.tr, c.tc + 16);
-    bin_pair2<T, UNI>(c, kp + ko + 16 * KP, fp + fo + 16 * BX, c.tr + 16, c.tc);
-    bin_pair2<T, UNI>(c, kp + ko + 16 * KP + 16, fp + fo + 16 * BX + 32, c.tr + 16, c.tc + 16);
+    bin_pair2<T, UNI>(c, kp + ko, fp + fo, c.emask & 3u);
+    bin_pair2<T, UNI>(c, kp + ko + 16, fp + fo + 32, (c.emask >> 2) & 3u);
+    bin_pair2<T, UNI>(c, kp + ko + 16 * KP, fp + fo + 16 * BX, (c.emask >> 4) & 3u);
+    bin_pair2<T, UNI>(c, kp + ko + 16 * KP + 16, fp + fo + 16 * BX + 32, (c.emask >> 6) & 3u);
 #pragma unroll
     for (int e = 0; e < 2; e++) {
         const uint32_t lv = e ? c.left1 : c.left0;
         if (lv != ~0u && (lv >> 31) == q) {
             const int row = (int)(lv & 0xFFFFu), pair = (int)((lv >> 16) & 0x7FFFu);
-            bin_pair2<T, UNI>(c, kp + row * KP + pair, fp + row * BX + F0 + 2 * pair, row, pair);
+            bin_pair2<T, UNI>(c, kp + row * KP + pair, fp + row * BX + F0 + 2 * pair,
+                              c.edge ? out_mask(c, row, pair) : 0u);
         }
     }
 }
@@ -219,7 +321,7 @@ __device__ __forceinline__ void issue_plane(Ctx &c, const CUtensorMap *tmap, int
 // planes h+3, h+4; the block synchronises; thread 0 requests planes h+NS+1,
 // h+NS+2 into the slots of planes h+1, h+2 (binned at the previous barrier
 // step); the block bins planes h+3, h+4.  Returns false if the block must stop.
-template <typename T>
+template <typename T, bool RW>
 __device__ __forceinline__ bool barrier_step(Ctx &c, const CUtensorMap *tmap, int h, int L)
 {
     if (threadIdx.x == 0) {
@@ -246,12 +348,13 @@ __device__ __forceinline__ bool barrier_step(Ctx &c, const CUtensorMap *tmap, in
         if (threadIdx.x == 0) drain(c);
         return false;
     }
-    if (threadIdx.x == 0) {
+    if (RW || threadIdx.x == 0) {
 #pragma unroll
         for (int q = NS + 1; q <= NS + 2; q++) {
             const int pi = h + q;
             if (pi > c.z1) break;
-            issue_plane<T>(c, tmap, pi);
+            if constexpr (RW) issue_plane_rw(c, pi);
+            else issue_plane<T>(c, tmap, pi);
         }
     }
 #pragma unroll
@@ -261,6 +364,10 @@ __device__ __forceinline__ bool barrier_step(Ctx &c, const CUtensorMap *tmap, in
         uint32_t *kp = c.kring + (uint32_t)(pb & (NK - 1)) * KWORDS;
         if (pb < c.zv0 || pb >= c.zv1) {
             fill_never(kp, L);
+        } else if constexpr (RW) {
+            const float *fp = (const float *)(c.ring + (size_t)slot_of(c, pb) * SLOT_BYTES<float, true>());
+            if (c.fb.uniform) bin_plane_rw<true>(c, kp, fp, pb, (uint32_t)q);
+            else bin_plane_rw<false>(c, kp, fp, pb, (uint32_t)q);
         } else {
             const T *fp = (const T *)(c.ring + (size_t)slot_of(c, pb) * SLOT_BYTES<T>());
             if (sizeof(T) != 4 || c.fb.uniform) bin_plane<T, true>(c, kp, fp, (uint32_t)q);
@@ -349,14 +456,14 @@ __device__ __forceinline__ void half_step(Ctx &c, int *hist, Row5 (&P)[4], Row5 
 
 // The plane walk of one item (z0-4 .. z1-1 in barrier steps of two planes).
 // False when a bounded wait gave up (the block then returns).
-template <typename T, int DM, bool SKIP>
+template <typename T, int DM, bool SKIP, bool RW>
 __device__ __forceinline__ bool walk_item(Ctx &c, const CUtensorMap *tmap, int *hist, Row5 (&W0)[4],
                                           Row5 (&W1)[4], SliceState &sa, SliceState &sb, uint32_t &nbar, int L)
 {
     const int nsteps = c.z1 - c.z0 + 4;
     for (int t = 0; t < nsteps; t += 2) {
         const int h = c.z0 - 4 + t;
-        if (!barrier_step<T>(c, tmap, h, L)) return false;
+        if (!barrier_step<T, RW>(c, tmap, h, L)) return false;
         if (DM & 4) {
             if (++nbar == 3) {
                 nbar = 0;
@@ -369,24 +476,31 @@ __device__ __forceinline__ bool walk_item(Ctx &c, const CUtensorMap *tmap, int *
     return true;
 }
 
-template <typename T, int DM>
+template <typename T, int DM, bool RW>
 __global__ void __launch_bounds__(kThreads, 2) k_planar3d(const __grid_constant__ CUtensorMap tmap, Params p)
 {
     constexpr int hw = HW<T>();
     extern __shared__ __align__(128) unsigned char smem[];
     Ctx c;
     c.ring = smem;
-    c.kring = (uint32_t *)(smem + OFF_KEYS<T>());
-    c.bars = (uint64_t *)(smem + OFF_BARS<T>());
-    c.abort_flag = (volatile int *)(smem + OFF_BARS<T>() + NS * 8);
+    c.kring = (uint32_t *)(smem + OFF_KEYS<T, RW>());
+    c.bars = (uint64_t *)(smem + OFF_BARS<T, RW>());
+    c.abort_flag = (volatile int *)(smem + OFF_BARS<T, RW>() + NS * 8);
     c.err = p.err;
-    int *const hist = (int *)(smem + OFF_HIST<T>());
+    c.field = p.field;
+    c.nelem = p.nelem;
+    c.HW = p.H * p.W;
+    c.hw4 = (int)(c.HW & 3);
+    c.w4 = (int)(p.W & 3);
+    c.Hi = (int)p.H;
+    c.Wi = (int)p.W;
+    int *const hist = (int *)(smem + OFF_HIST<T, RW>());
     const int L = p.L;
     for (int i = threadIdx.x; i < hist_rows<DM>() * hw; i += kThreads) hist[i] = 0;
     c.fb = FBin{};
     c.fb.L = L;
     if constexpr (sizeof(T) == 4) {
-        float *const thr = (float *)(smem + off_thr<T, DM>());
+        float *const thr = (float *)(smem + off_thr<T, DM, RW>());
         for (int k = threadIdx.x; k < L; k += kThreads) thr[k] = p.thr[k];
         c.fb.t = thr;
         c.fb.t0 = p.thr[0];
@@ -402,7 +516,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_planar3d(const __grid_constant_
         }
     }
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NS; i++) fast3d::mbar_init(&c.bars[i], 1);
+        // row copies: one (no-increment) arrival per thread tracks its cp.async copies
+        for (int i = 0; i < NS; i++) fast3d::mbar_init(&c.bars[i], RW ? kThreads : 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *c.abort_flag = 0;
     }
@@ -433,20 +548,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_planar3d(const __grid_constant_
         c.z1 = min(c.z0 + p.tz, p.zc1);
         // binned cells x0-2 .. x0+65, y0-1 .. y0+32
         c.edge = c.x0 < 2 || c.x0 + 66 > p.W || c.y0 < 1 || c.y0 + 33 > p.H;
+        c.emask = 0;
+        if (c.edge && (sizeof(T) == 2 || RW))
+            c.emask = out_mask(c, c.tr, c.tc) | out_mask(c, c.tr, c.tc + 16) << 2 |
+                      out_mask(c, c.tr + 16, c.tc) << 4 | out_mask(c, c.tr + 16, c.tc + 16) << 6;
         __syncthreads();   // the previous item is done with both rings
         c.base = seq;
-        if (threadIdx.x == 0) {
+        if (RW || threadIdx.x == 0) {
             for (int q = 0; q < NS - 2; q++) {
                 const int pz = c.z0 - 1 + q;
                 if (pz > c.z1) break;
-                issue_plane<T>(c, &tmap, pz);
+                if constexpr (RW) issue_plane_rw(c, pz);
+                else issue_plane<T>(c, &tmap, pz);
             }
         }
         // counted voxels x0 .. x0+63, y0 .. y0+31: past the field's edge the
         // walk leaves out voxels at level L
         const bool skip = c.x0 + TX > p.W || c.y0 + TY > p.H;
-        const bool ok = skip ? walk_item<T, DM, true>(c, &tmap, hist, W0, W1, sa, sb, nbar, L)
-                             : walk_item<T, DM, false>(c, &tmap, hist, W0, W1, sa, sb, nbar, L);
+        const bool ok = skip ? walk_item<T, DM, true, RW>(c, &tmap, hist, W0, W1, sa, sb, nbar, L)
+                             : walk_item<T, DM, false, RW>(c, &tmap, hist, W0, W1, sa, sb, nbar, L);
         if (!ok) return;
         seq += (uint32_t)(c.z1 - c.z0 + 2);
     }
@@ -493,11 +613,11 @@ static int plan_tile_z(int64_t columns, int planes, int grid)
     return best;
 }
 
-template <typename T, int DM>
+template <typename T, int DM, bool RW = false>
 static int launch_dm(const CUtensorMap &map, Params p, int tile_z, int num_sms, int grid_override, cudaStream_t s)
 {
-    auto kern = k_planar3d<T, DM>;
-    const size_t smem = smem_bytes<T, DM>();
+    auto kern = k_planar3d<T, DM, RW>;
+    const size_t smem = smem_bytes<T, DM, RW>();
     EC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
@@ -530,9 +650,12 @@ bool planar_3d_supported(const void *field, const int64_t dims[3], int dtype, co
                      (desc == 1u || desc == 13u || desc == 15u);
     const bool u16 = dtype == EC_U16 && !thr && L >= 1 && L <= LCAP<uint16_t>() && (desc == 1u || desc == 9u);
     if (!f32 && !u16) return false;
-    const int esz = f32 ? 4 : 2;
-    return (dims[2] * esz) % 16 == 0 && ((uintptr_t)field % 16) == 0 && dims[0] <= INT32_MAX / 2 &&
-           dims[1] <= INT32_MAX / 2 && dims[2] <= INT32_MAX / 2;
+    if (((uintptr_t)field % 16) != 0 || dims[0] > INT32_MAX / 2 || dims[1] > INT32_MAX / 2 ||
+        dims[2] > INT32_MAX / 2)
+        return false;
+    // float32 rows of any width (tensor map, or row copies when a row is not
+    // a multiple of 16 bytes); uint16 rows through the tensor map only
+    return f32 || (dims[2] * 2) % 16 == 0;
 }
 
 int launch_planar_3d(const void *field, const int64_t dims[3], const BinArgs &ba, const HistArgs &ha, int tile_z,
@@ -545,8 +668,9 @@ int launch_planar_3d(const void *field, const int64_t dims[3], const BinArgs &ba
     if (!planar_3d_supported(field, dims, ba.dtype, ba.thr, ba.L, desc)) return EC_ERR_UNSUPPORTED;
     const bool f32 = ba.dtype == EC_F32;
     const int esz = f32 ? 4 : 2;
+    const bool rw = f32 && (dims[2] * 4) % 16 != 0;   // row copies instead of the tensor map
     PFN_cuTensorMapEncodeTiled_v12000 enc = (PFN_cuTensorMapEncodeTiled_v12000)tma_encode_fn();
-    if (!enc) return EC_ERR_UNSUPPORTED;
+    if (!enc && !rw) return EC_ERR_UNSUPPORTED;
     Params p{};
     p.D = dims[0]; p.H = dims[1]; p.W = dims[2];
     p.zc0 = zrange ? zrange[0] : 0;
@@ -563,8 +687,19 @@ int launch_planar_3d(const void *field, const int64_t dims[3], const BinArgs &ba
     p.err = err_flag;
     p.uni = err_flag + 2;
     p.test_give_up = ha.test_give_up;
+    p.field = (const float *)field;
+    p.nelem = dims[0] * dims[1] * dims[2];
     CUtensorMap map;
     memset(&map, 0, sizeof map);
+    if (rw) {
+        if (!ba.uni_ready) {
+            const int rc = launch_uniform_check((const float *)ba.thr, ba.L, err_flag + 2, s);
+            if (rc) return rc;
+        }
+        if (desc == 1u) return launch_dm<float, 1, true>(map, p, tile_z, num_sms, grid_override, s);
+        if (desc == 13u) return launch_dm<float, 13, true>(map, p, tile_z, num_sms, grid_override, s);
+        return launch_dm<float, 15, true>(map, p, tile_z, num_sms, grid_override, s);
+    }
     cuuint64_t gdim[3] = {(cuuint64_t)p.W, (cuuint64_t)p.H, (cuuint64_t)p.D};
     cuuint64_t gstride[2] = {(cuuint64_t)(p.W * esz), (cuuint64_t)(p.W * p.H * esz)};
     cuuint32_t box[3] = {(cuuint32_t)(f32 ? BXT<float>() : BXT<uint16_t>()), (cuuint32_t)BY, 1};
