@@ -247,8 +247,8 @@ __device__ __forceinline__ void bin_plane_rw(const Ctx &c, uint32_t *kp, const f
 // x0 - 4 of the row (646 chunks, thread t takes chunks t, t + 256, t + 512).
 // A chunk is one cp.async; the part of a chunk outside the field's memory is
 // zero-filled (those positions lie outside the field and are binned to L).
-// Rows and planes outside the field are not read.  Each thread then makes
-// the slot's barrier (expecting one arrival per thread) track its copies.
+// Rows and planes outside the field are not read.  The caller closes the
+// copies of two planes as one cp.async group.
 __device__ __forceinline__ void issue_plane_rw(Ctx &c, int plane)
 {
     constexpr int CPR = RPITCH / 4;   // chunks per row
@@ -272,9 +272,6 @@ __device__ __forceinline__ void issue_plane_rw(Ctx &c, int plane)
             }
         }
     }
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(fast3d::smem_u32(&c.bars[s]))
-                 : "memory");
-    if (threadIdx.x == 0) c.inflight |= 1u << s;
 }
 
 // Bin one staged plane (q = 0: the first of the barrier step, 1: the second):
@@ -324,7 +321,10 @@ __device__ __forceinline__ void issue_plane(Ctx &c, const CUtensorMap *tmap, int
 template <typename T, bool RW>
 __device__ __forceinline__ bool barrier_step(Ctx &c, const CUtensorMap *tmap, int h, int L)
 {
-    if (threadIdx.x == 0) {
+    if constexpr (RW) {
+        // planes h+3, h+4 are the older of this thread's two open groups
+        fast3d::cp_async_wait<1>();
+    } else if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 3; q <= 4; q++) {
             const int pb = h + q;
@@ -344,7 +344,7 @@ __device__ __forceinline__ bool barrier_step(Ctx &c, const CUtensorMap *tmap, in
         }
     }
     __syncthreads();
-    if (*c.abort_flag) {
+    if (!RW && *c.abort_flag) {
         if (threadIdx.x == 0) drain(c);
         return false;
     }
@@ -356,6 +356,7 @@ __device__ __forceinline__ bool barrier_step(Ctx &c, const CUtensorMap *tmap, in
             if constexpr (RW) issue_plane_rw(c, pi);
             else issue_plane<T>(c, tmap, pi);
         }
+        if constexpr (RW) fast3d::cp_async_commit();   // one group per barrier step, possibly empty
     }
 #pragma unroll
     for (int q = 0; q < 2; q++) {
@@ -516,8 +517,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_planar3d(const __grid_constant_
         }
     }
     if (threadIdx.x == 0) {
-        // row copies: one (no-increment) arrival per thread tracks its cp.async copies
-        for (int i = 0; i < NS; i++) fast3d::mbar_init(&c.bars[i], RW ? kThreads : 1);
+        for (int i = 0; i < NS; i++) fast3d::mbar_init(&c.bars[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *c.abort_flag = 0;
     }
@@ -554,12 +554,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_planar3d(const __grid_constant_
                       out_mask(c, c.tr + 16, c.tc) << 4 | out_mask(c, c.tr + 16, c.tc + 16) << 6;
         __syncthreads();   // the previous item is done with both rings
         c.base = seq;
-        if (RW || threadIdx.x == 0) {
+        if constexpr (RW) {
+            // planes z0-1, z0 and z0+1, z0+2 as two groups
+            for (int q = 0; q < NS - 2; q++) {
+                const int pz = c.z0 - 1 + q;
+                if (pz <= c.z1) issue_plane_rw(c, pz);
+                if (q & 1) fast3d::cp_async_commit();
+            }
+        } else if (threadIdx.x == 0) {
             for (int q = 0; q < NS - 2; q++) {
                 const int pz = c.z0 - 1 + q;
                 if (pz > c.z1) break;
-                if constexpr (RW) issue_plane_rw(c, pz);
-                else issue_plane<T>(c, &tmap, pz);
+                issue_plane<T>(c, &tmap, pz);
             }
         }
         // counted voxels x0 .. x0+63, y0 .. y0+31: past the field's edge the
