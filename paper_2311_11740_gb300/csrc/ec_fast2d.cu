@@ -43,10 +43,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_pixel2d_fast(Params p)
     if (ROWS != ROWS_LOADS) tail += (size_t)NRAW * raw_bytes<T>();
     const int L = p.L;
     c.sh_hist = nullptr;
+    const int slots = hist_slots2<DM>(p.nd);
     if (p.smem_hist) {
         c.sh_hist = (int *)tail;
-        for (int i = threadIdx.x; i < p.nd * (L + 1); i += kThreads) c.sh_hist[i] = 0;
-        tail += ((size_t)p.nd * (L + 1) * 4 + 15) & ~(size_t)15;
+        for (int i = threadIdx.x; i < slots * (L + 1); i += kThreads) c.sh_hist[i] = 0;
+        tail += ((size_t)slots * (L + 1) * 4 + 15) & ~(size_t)15;
     }
     c.fb = FBin{};
     c.ib = IBin<T>{};
@@ -127,13 +128,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_pixel2d_fast(Params p)
         }
     }
     if (c.sh_hist) {
+        if constexpr (DM == 7) {
+            __syncthreads();
+            exchange_packed2(c.sh_hist, L);
+        }
         __syncthreads();
         for (int i = threadIdx.x; i < p.nd * L; i += kThreads) {
-            // global rows are [nd][L]; compile-time rows are interleaved [L+1][nd]
+            // global rows are [nd][L]; compile-time rows are interleaved [L+1][slots]
+            // (DM 7: EC, packed, perimeter, area, spare)
             int v;
             if constexpr (DM != 0) {
                 const int r = i / L, k = i - r * L;
-                v = c.sh_hist[k * p.nd + r];
+                v = c.sh_hist[k * slots + (DM == 7 && r > 0 ? r + 1 : r)];
             } else {
                 v = c.sh_hist[i];
             }
@@ -167,7 +173,12 @@ static int launch_dt(const Params &p, uint32_t desc, size_t smem, int num_sms, i
 {
     if (p.smem_hist && !p.conn4) {
         if (desc == 1u) return launch_t<T, false, 1>(p, smem, num_sms, items, grid, rows, s);
-        if (desc == 7u) return launch_t<T, false, 7>(p, smem, num_sms, items, grid, rows, s);
+        if (desc == 7u && (size_t)5 * ((size_t)p.L + 1) * 4 <= kSmemHistBudget) {
+            // five words per level instead of the three rows
+            const size_t extra = (((size_t)5 * (p.L + 1) * 4 + 15) & ~(size_t)15) -
+                                 (((size_t)3 * (p.L + 1) * 4 + 15) & ~(size_t)15);
+            return launch_t<T, false, 7>(p, smem + extra, num_sms, items, grid, rows, s);
+        }
     }
     return p.conn4 ? launch_t<T, true>(p, smem, num_sms, items, grid, rows, s)
                    : launch_t<T, false>(p, smem, num_sms, items, grid, rows, s);

@@ -77,6 +77,7 @@ struct Ctx2 {
     int x0, y0, y1;
     bool interior;
     int nb = 1;          // row bands side by side in the strip (banded walk when > 1)
+    int since = 0;       // rows counted since the packed words were last exchanged (DM 7)
     int64_t yb0 = 0;     // first field row of band 0; band b, virtual row v -> row yb0 + b*kBandRows + v
 };
 
@@ -136,6 +137,45 @@ __device__ __forceinline__ void bin_row(Ctx2<T> &c, int64_t y, const RowRaw<T> &
 template <int DM, int D>
 constexpr int dm_row2() { return ((DM & 1) && D > 0) + ((DM & 2) && D > 1); }
 
+// EC + perimeter + area with compile-time rows (DM 7) keep five words per
+// level (an odd stride spreads a warp's levels over the banks): EC
+// (atomics), a packed word (atomics: bits 0-16 add 4 - #edge neighbours
+// preceding, bits 17-31 count pixels), the perimeter and area decoded from
+// it (perimeter = 2 * sum - 4 * count, area = count), and a spare word.  The packed
+// words are exchanged to zero at least every kExchangeRows rows of a block
+// (plus at most one row of skew between its threads), so a word collects at
+// most 14 * 1024 < 2^15 pixels and 4 * 2^15 <= 2^17 between exchanges.
+template <int DM>
+constexpr int hist_slots2(int nd) { return DM == 7 ? 5 : nd; }
+constexpr int kExchangeRows = 12;
+
+// Exchange this thread's share of the packed words (levels tid, tid + 256,
+// ...) and add them into the perimeter and area words of their levels.
+__device__ __forceinline__ void exchange_packed2(int *h, int L)
+{
+    for (int k = threadIdx.x; k <= L; k += kThreads) {
+        const uint32_t w = atomicExch((unsigned int *)(h + 5 * k + 1), 0u);
+        if (w) {
+            const int n = (int)(w >> 17), sum = (int)(w & 0x1FFFFu);
+            h[5 * k + 2] += 2 * sum - 4 * n;
+            h[5 * k + 3] += n;
+        }
+    }
+}
+
+// After a group of rows: exchange the packed words when due.
+template <int DM, typename T>
+__device__ __forceinline__ void after_rows(Ctx2<T> &c, int rows)
+{
+    if constexpr (DM == 7) {
+        c.since += rows;
+        if (c.since >= kExchangeRows) {
+            c.since = 0;
+            exchange_packed2(c.sh_hist, c.p.L);
+        }
+    }
+}
+
 // Load row y+1 into window slot (R+1)%3 (R = position of row y) and count
 // row y if it belongs to the item.  SKIP (strips whose counted columns reach
 // past the field): pixels at the never-active level L are left out of the
@@ -173,15 +213,21 @@ __device__ __forceinline__ void count_row(Ctx2<T> &c, uint32_t (&win)[3][5], int
         if constexpr (DM != 0) {
             // interleaved rows [L+1][ND] (the never-active level L has its own,
             // discarded slot): one address per pixel, rows at immediate offsets
-            constexpr int ND = (DM & 1) + ((DM >> 1) & 1) + ((DM >> 2) & 1);
+            constexpr int ND = hist_slots2<DM>((DM & 1) + ((DM >> 1) & 1) + ((DM >> 2) & 1));
             int *const h = c.sh_hist;
 #pragma unroll
             for (int v = 0; v < 4; v++) {
                 if (SKIP && key[v] >= (uint32_t)L) continue;
                 int *const e = h + key[v] * ND;
-                if (DM & 1) atomicAdd(e + dm_row2<DM, 0>(), ecv[v]);
-                if (DM & 2) atomicAdd(e + dm_row2<DM, 1>(), pev[v]);
-                if (DM & 4) atomicAdd(e + dm_row2<DM, 2>(), 1);
+                if constexpr (DM == 7) {
+                    atomicAdd(e, ecv[v]);
+                    // (perimeter change + 4) / 2 = 4 - #edge neighbours preceding, and one pixel
+                    atomicAdd((unsigned int *)(e + 1), (uint32_t)((pev[v] + 4) >> 1) | (1u << 17));
+                } else {
+                    if (DM & 1) atomicAdd(e + dm_row2<DM, 0>(), ecv[v]);
+                    if (DM & 2) atomicAdd(e + dm_row2<DM, 1>(), pev[v]);
+                    if (DM & 4) atomicAdd(e + dm_row2<DM, 2>(), 1);
+                }
             }
         } else {
 #pragma unroll
@@ -365,6 +411,7 @@ __device__ __forceinline__ void walk_item_2d(Ctx2<T> &c, uint32_t (&win)[3][5])
         ystep<T, CONN4, 0, DM, SKIP>(c, win, raw, t);
         if (t + 1 < nsteps) ystep<T, CONN4, 1, DM, SKIP>(c, win, raw, t + 1);
         if (t + 2 < nsteps) ystep<T, CONN4, 2, DM, SKIP>(c, win, raw, t + 2);
+        after_rows<DM>(c, 3);
     }
 }
 
@@ -380,6 +427,7 @@ __device__ __forceinline__ void walk_item_2d_async(Ctx2<T> &c, uint32_t (&win)[3
         ystep_async<T, CONN4, 0, DM, STG, BANDED, SKIP>(c, win, t);
         if (t + 1 < nsteps) ystep_async<T, CONN4, 1, DM, STG, BANDED, SKIP>(c, win, t + 1);
         if (t + 2 < nsteps) ystep_async<T, CONN4, 2, DM, STG, BANDED, SKIP>(c, win, t + 2);
+        after_rows<DM>(c, 3);
     }
     cp_async_wait<0>();
 }
