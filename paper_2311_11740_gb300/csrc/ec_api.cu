@@ -6,7 +6,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <thread>
 #include <vector>
@@ -158,6 +160,30 @@ int64_t selfcheck_planar(const Table3D &t3)
 }
 
 }  // namespace
+
+int ec::kernel_occupancy(const void *kern, int threads, size_t smem, int *occ)
+{
+    int dev = 0;
+    EC_CUDA(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
+    static std::map<std::pair<int, const void *>, size_t> limit;   // dynamic shared bytes allowed so far
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(dev, kern, threads, smem);
+    const auto it = cache.find(key);
+    if (it != cache.end()) {
+        *occ = it->second;
+        return EC_OK;
+    }
+    size_t &lim = limit[std::make_pair(dev, kern)];
+    if (smem > lim) {
+        EC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        lim = smem;
+    }
+    EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, threads, smem));
+    cache[key] = *occ;
+    return EC_OK;
+}
 
 int ec::ensure_scratch(ec_ctx *ctx, size_t bytes)
 {

@@ -720,9 +720,8 @@ static int batch_run(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, cudaSt
     // ---- launch configuration
     const size_t hist_cap = std::max<size_t>(max_smem_entries, 1);
     const size_t smem = batch_smem_bytes(hist_cap);
-    EC_CUDA(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kThreads, smem));
+    if (const int orc = kernel_occupancy((const void *)k_batch, kThreads, smem, &occ)) return orc;
     if (occ < 1) { set_error("batch kernel does not fit (%zu B shared)", smem); return EC_ERR_UNSUPPORTED; }
     int grid = plan.grid > 0 ? std::min(plan.grid, ctx->num_sms * occ) : ctx->num_sms * occ;
     grid = std::min<int>(grid, (int)items.size());

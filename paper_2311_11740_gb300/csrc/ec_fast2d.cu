@@ -156,9 +156,8 @@ static int launch_t(const Params &p, size_t smem, int num_sms, int items, int gr
                 : rows == ROWS_COVER ? k_pixel2d_fast<T, CONN4, DM, ROWS_COVER>
                                      : k_pixel2d_fast<T, CONN4, DM, ROWS_LOADS>;
     if (rows != ROWS_LOADS) smem += (size_t)NRAW * raw_bytes<T>();
-    EC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
+    if (const int orc = kernel_occupancy((const void *)kern, kThreads, smem, &occ)) return orc;
     if (occ < 1) { set_error("fast 2D kernel does not fit (%zu B shared)", smem); return EC_ERR_UNSUPPORTED; }
     int grid = grid_override > 0 ? grid_override : num_sms * occ;
     grid = grid > items ? items : grid;

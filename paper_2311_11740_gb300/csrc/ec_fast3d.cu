@@ -328,9 +328,8 @@ static int launch_t(const CUtensorMap &map, const Params &p, size_t smem, int nu
                     cudaStream_t s)
 {
     auto kern = k_voxel3d_fast<T, MODE, PER, DM, SCHED, SLICE>;
-    EC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
+    if (const int orc = kernel_occupancy((const void *)kern, kThreads, smem, &occ)) return orc;
     if (occ < 1) { set_error("fast 3D kernel does not fit (%zu B shared)", smem); return EC_ERR_UNSUPPORTED; }
     int grid = grid_override > 0 ? grid_override : num_sms * occ;
     grid = grid > items ? items : grid;

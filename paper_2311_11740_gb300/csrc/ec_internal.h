@@ -112,14 +112,15 @@ int validate_request(int ndim, const void *field, const int64_t *dims, int dtype
 // Sets the device for a scope and restores the caller's afterwards.
 struct DeviceGuard {
     int prev = -1;
+    bool switched = false;
     explicit DeviceGuard(int dev)
     {
         if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
+        if (prev != dev) switched = cudaSetDevice(dev) == cudaSuccess;
     }
     ~DeviceGuard()
     {
-        if (prev >= 0) cudaSetDevice(prev);
+        if (switched && prev >= 0) cudaSetDevice(prev);
     }
 };
 
@@ -166,6 +167,11 @@ int enqueue_curve(const CurvePlan &plan, int ndim, const void *field, const int6
                   cudaStream_t s);
 // Grow the context's scratch to at least `bytes` (device-synchronising when it grows).
 int ensure_scratch(ec_ctx *ctx, size_t bytes);
+// Blocks of `kern` (threads per block, dynamic shared bytes) resident per SM
+// on the current device, with the kernel's dynamic shared-memory limit raised
+// as needed.  Cached per device, kernel and size (the queries cost host time
+// on every small request otherwise).
+int kernel_occupancy(const void *kern, int threads, size_t smem, int *occ);
 // Autotuner (EC_OPT_AUTOTUNE): fill `plan` from the cache, timing the
 // candidate plans on this request first when its shape class is new.
 int tuned_plan(ec_ctx *ctx, int ndim, const void *field, const int64_t *dims, int dtype, const void *thr,

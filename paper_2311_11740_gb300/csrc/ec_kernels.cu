@@ -512,9 +512,8 @@ __global__ void k_check_sorted_int(const T *t, int L, int *flag)
 template <typename KernelT>
 static int prepare_kernel(KernelT kernel, size_t smem, int num_sms, int items, int grid_override, int *grid_out)
 {
-    EC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem));
+    if (const int orc = kernel_occupancy((const void *)kernel, kThreads, smem, &occ)) return orc;
     if (occ < 1) {
         set_error("kernel does not fit on an SM (%zu bytes of shared memory)", smem);
         return EC_ERR_UNSUPPORTED;

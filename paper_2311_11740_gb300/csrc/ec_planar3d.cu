@@ -624,9 +624,8 @@ static int launch_dm(const CUtensorMap &map, Params p, int tile_z, int num_sms, 
 {
     auto kern = k_planar3d<T, DM, RW>;
     const size_t smem = smem_bytes<T, DM, RW>();
-    EC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
+    if (const int orc = kernel_occupancy((const void *)kern, kThreads, smem, &occ)) return orc;
     if (occ < 1) { set_error("planar 3D kernel does not fit (%zu B shared)", smem); return EC_ERR_UNSUPPORTED; }
     int grid = grid_override > 0 ? grid_override : num_sms * occ;
     const int planes = p.zc1 - p.zc0;

@@ -357,9 +357,8 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_types2(G2 g, const T *thr, in
 template <typename KernelT>
 int grid_for(KernelT kernel, size_t smem, int num_sms, int64_t items, int grid_override, int *grid)
 {
-    EC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    EC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kTmThreads, smem));
+    if (const int orc = kernel_occupancy((const void *)kernel, kTmThreads, smem, &occ)) return orc;
     if (occ < 1) { set_error("type-map kernel does not fit on an SM (%zu B shared)", smem); return EC_ERR_UNSUPPORTED; }
     int64_t gr = grid_override > 0 ? grid_override : (int64_t)num_sms * occ;
     if (gr > items) gr = items;
