@@ -234,10 +234,11 @@ int ec_batch_tuned_plan(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, int
 
 /* ----------------------------------------------------- workload generator
  * The hash-box field of the low-memory workload (input generation only):
- * with m the 32-bit finaliser of MurmurHash3 and a = m(lo32(seed) ^
- * m(hi32(seed))), h(x,y,z) = low 16 bits of m(m(m(a ^ z) ^ y) ^ x) (x, y, z
- * taken mod 2^32); v = floor(sum of h over the 5x5x5 box around (x,y,z) /
- * 2000), in [0, 4095], defined for every integer coordinate.  ec_gen_hashbox_u16 writes the nz x ny x nx box with origin
+ * with m the 32-bit finaliser of MurmurHash3, a = m(lo32(seed) ^
+ * m(hi32(seed))) and u = m(m(m(a ^ z) ^ y) ^ floor(x/2)) (taken mod 2^32),
+ * h(x,y,z) = the low 16 bits of u for even x, its high 16 bits for odd x;
+ * v = floor(sum of h over the 5x5x5 box around (x,y,z) / 2000), in
+ * [0, 4095], defined for every integer coordinate.  ec_gen_hashbox_u16 writes the nz x ny x nx box with origin
  * (x0, y0, z0) to dst_dev (uint16, C-contiguous) on `stream`.
  * ec_hashbox_producer is an ec_slab_fn: with user -> ec_hashbox_spec it
  * writes planes [z0, z1) of the box (relative to spec->z0) for

@@ -410,7 +410,9 @@ int oracle_ec_dual_2d(const int32_t *bins, int64_t h, int64_t w, int32_t L, int6
  * u ^= u >> 13; u *= 0xC2B2AE35; u ^= u >> 16), called m below.
  *
  * a        = m(lo32(seed) ^ m(hi32(seed)))
- * h(x,y,z) = low 16 bits of m(m(m(a ^ z) ^ y) ^ x)      (x, y, z mod 2^32)
+ * u(p,y,z) = m(m(m(a ^ z) ^ y) ^ p)                     (p, y, z mod 2^32)
+ * h(x,y,z) = low 16 bits of u(floor(x/2), y, z) for even x, high 16 bits
+ *            for odd x
  * v(x,y,z) = floor( sum_{|dx|,|dy|,|dz| <= 2} h(x+dx, y+dy, z+dz) * 4096
  *                   / (125 * 65536) )                       in [0, 4095]
  * defined for all integer coordinates (no border case).
@@ -430,7 +432,9 @@ static uint32_t hash16(uint64_t seed, int64_t x, int64_t y, int64_t z)
     const uint32_t a = murmur_fmix32((uint32_t)seed ^ murmur_fmix32((uint32_t)(seed >> 32)));
     const uint32_t hz = murmur_fmix32(a ^ (uint32_t)z);
     const uint32_t hy = murmur_fmix32(hz ^ (uint32_t)y);
-    return murmur_fmix32(hy ^ (uint32_t)x) & 0xFFFFu;
+    const int64_t p = (x - (x & 1)) / 2;   /* floor(x / 2) */
+    const uint32_t u = murmur_fmix32(hy ^ (uint32_t)p);
+    return (x & 1) ? (u >> 16) : (u & 0xFFFFu);
 }
 
 int oracle_hashbox_u16(uint64_t seed, int64_t x0, int64_t y0, int64_t z0,

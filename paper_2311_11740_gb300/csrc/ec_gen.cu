@@ -5,15 +5,18 @@
 //   m(u)     = MurmurHash3's 32-bit finaliser (Appleby): u ^= u >> 16;
 //              u *= 0x85EBCA6B; u ^= u >> 13; u *= 0xC2B2AE35; u ^= u >> 16
 //   a        = m(lo32(seed) ^ m(hi32(seed)))
-//   h(x,y,z) = low 16 bits of m(m(m(a ^ z) ^ y) ^ x)    (x, y, z mod 2^32)
+//   u(p,y,z) = m(m(m(a ^ z) ^ y) ^ p)                   (p, y, z mod 2^32)
+//   h(x,y,z) = low 16 bits of u(floor(x/2), y, z) for even x, its high
+//              16 bits for odd x (one finaliser serves two neighbours)
 //   v(x,y,z) = floor( sum over the 5x5x5 box around (x,y,z) of h / 2000 )
 // (4096 / (125 * 65536) = 1 / 2000, so v lies in [0, 4095]).  The field is
 // defined for every integer coordinate, so any sub-box can be generated.
 //
 // One block produces a 64 x 32 column of outputs and walks it along z.  Per
 // input plane: the 68 x 36 hashes of its neighbourhood go to shared memory
-// (1.2 hashes per output; the per-row keys m(m(a ^ z) ^ y) are formed one
-// plane ahead by 36 threads), 5-wide sums along x are formed four at a time
+// (0.6 finalisers per output, a thread taking a 10-wide run of one row; the
+// per-row keys m(m(a ^ z) ^ y) are formed one plane ahead by 36 threads),
+// 5-wide sums along x are formed four at a time
 // as running sums, each thread sums 5 rows of those for its 4 x 2 outputs,
 // and a running sum over the last five planes (a register ring indexed at
 // compile time: the plane loop is unrolled by five) gives the sum along z.
@@ -42,6 +45,7 @@ struct GenCtx {
     int64_t ox, oy, oz, nx, ny, nz, bx0, by0;
     int tx, ty;
     int hrow, hseg;          // this thread's hash row and 10-wide segment (hrow >= HY: none)
+    bool odd;                // the tile's first hashed x (ox + bx0 - 2) is odd (the same for every segment)
     uint16_t *out[2];        // output rows 2ty, 2ty+1 of plane 0 at x = bx0 + 4tx (nullptr: past the box)
     int64_t plane;           // elements per output plane
     bool vec;                // four outputs as one 8-byte store
@@ -64,12 +68,29 @@ __device__ __forceinline__ void gen_plane(const GenCtx &g, int64_t k, uint32_t (
                                           uint32_t (*rk)[HY], uint32_t (&ring)[5][8], uint32_t (&zs)[8])
 {
     if (g.hrow < HY) {
-        // ten consecutive hashes of one row (the padding columns 68..71 are never read)
+        // ten consecutive hashes of one row (the padding columns 68..71 are never read):
+        // halves of the finalisers of pairs floor(x/2) .. floor(x/2) + 4 (+ 5 when x starts odd)
         const uint32_t key = rk[k & 1][g.hrow];
-        const uint32_t x0 = (uint32_t)(g.ox + g.bx0 - 2) + (uint32_t)(SEG * g.hseg);
+        const int64_t xs = g.ox + g.bx0 - 2 + SEG * g.hseg;
+        const uint32_t p0 = (uint32_t)((xs - (xs & 1)) / 2);
         uint32_t *row = &hs[g.hrow][SEG * g.hseg];
+        if (!g.odd) {
 #pragma unroll
-        for (int j = 0; j < SEG; j++) row[j] = fmix32(key ^ (x0 + (uint32_t)j)) & 0xFFFFu;
+            for (int j = 0; j < SEG / 2; j++) {
+                const uint32_t u = fmix32(key ^ (p0 + (uint32_t)j));
+                row[2 * j] = u & 0xFFFFu;
+                row[2 * j + 1] = u >> 16;
+            }
+        } else {
+            row[0] = fmix32(key ^ p0) >> 16;
+#pragma unroll
+            for (int j = 1; j < SEG / 2; j++) {
+                const uint32_t u = fmix32(key ^ (p0 + (uint32_t)j));
+                row[2 * j - 1] = u & 0xFFFFu;
+                row[2 * j] = u >> 16;
+            }
+            row[SEG - 1] = fmix32(key ^ (p0 + (uint32_t)(SEG / 2))) & 0xFFFFu;
+        }
     }
     __syncthreads();
     row_keys(g, k + 1, rk[(k + 1) & 1]);   // next plane's keys (read after the next barrier)
@@ -136,6 +157,7 @@ __global__ void __launch_bounds__(256, 3) k_hashbox(uint64_t seed, int64_t ox, i
     g.ty = threadIdx.x >> 4;   // outputs y 2ty, 2ty+1
     g.hrow = threadIdx.x / NSEG;
     g.hseg = threadIdx.x - g.hrow * NSEG;
+    g.odd = ((ox + g.bx0 - 2) & 1) != 0;
     g.plane = ny * nx;
     const int64_t x = g.bx0 + 4 * g.tx;
     for (int yy = 0; yy < 2; yy++) {

@@ -390,6 +390,7 @@ def test_hashbox_matches_definition():
         for dz, dy, dx in itertools.product(range(-2, 3), repeat=3):
             hz = _fmix32(a ^ ((z + dz) & 0xFFFFFFFF))
             hy = _fmix32(hz ^ ((y + dy) & 0xFFFFFFFF))
-            s += _fmix32(hy ^ ((x + dx) & 0xFFFFFFFF)) & 0xFFFF
+            u = _fmix32(hy ^ (((x + dx) // 2) & 0xFFFFFFFF))
+            s += (u >> 16) if (x + dx) % 2 else (u & 0xFFFF)
         assert got[k, j, i] == (s * 4096) // (125 * 65536)
     assert got.max() < 4096
