@@ -132,6 +132,37 @@ def test_planar_tma_uint16_identity_levels(ctx, shape):
         np.testing.assert_array_equal(got, oracle.ec_curves(g, None, 4096, 26, 9))
 
 
+# float32 rows that are not a multiple of 16 bytes: the planar kernel stages
+# each row itself (16-byte cp.async chunks from the boundary at or below the
+# row's first staged element, binned from the row's start phase; cells past
+# the row read neighbouring rows' values and are masked by coordinates).
+# Widths of every residue mod 4, partial tiles, the field's first and last
+# rows (chunks before and past its memory), item depths, and streamed slabs.
+SHAPES3_ROWS = [(1, 1, 5), (3, 33, 65), (17, 31, 131), (70, 65, 67), (5, 2, 197), (33, 97, 101), (2, 70, 130),
+                (9, 64, 3)]
+
+
+@pytest.mark.parametrize("shape", SHAPES3_ROWS)
+@pytest.mark.parametrize("uniform", [True, False])
+def test_planar_row_copies(ctx, shape, uniform):
+    rng = np.random.default_rng(zlib.crc32(repr((shape, uniform, "rows")).encode()))
+    if uniform:
+        f = workloads.grf_nd(int(rng.integers(1 << 30)), shape, 1.5).numpy().astype(np.float32)
+        L = int(rng.integers(2, 1025))
+        thr = workloads.uniform_thresholds(float(f.min()), float(f.max()), L).numpy()
+    else:
+        f = rng.normal(size=shape).astype(np.float32)
+        L = int(rng.integers(1, 1025))
+        thr = np.sort(rng.normal(size=L)).astype(np.float32)
+    for desc in (1, 13, 15):
+        check(ctx, f, thr, L, desc=desc, algos=[ec.ALGO_PLANAR])
+    if shape[0] >= 17:
+        check(ctx, f, thr, L, desc=13, algos=[ec.ALGO_PLANAR], tile_z=3)
+        for slab in (1, 7):
+            got = ec.curve_3d_stream(f, thresholds=thr, descriptors=13, slab_planes=slab, ctx=ctx)
+            np.testing.assert_array_equal(got, oracle.ec_curves(f, thr, L, 26, 13))
+
+
 def test_planar_tma_item_depths_and_constant_field(ctx):
     """Work items of 1..7 and 64 planes; a constant field puts every voxel of a
     block on one level, the largest count the packed area/volume words take
