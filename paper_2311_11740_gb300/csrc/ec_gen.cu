@@ -12,14 +12,17 @@
 // (4096 / (125 * 65536) = 1 / 2000, so v lies in [0, 4095]).  The field is
 // defined for every integer coordinate, so any sub-box can be generated.
 //
-// One block produces a 64 x 32 column of outputs and walks it along z.  Per
-// input plane: the 68 x 36 hashes of its neighbourhood go to shared memory
-// (0.6 finalisers per output, a thread taking a 10-wide run of one row; the
-// per-row keys m(m(a ^ z) ^ y) are formed one plane ahead by 36 threads),
-// 5-wide sums along x are formed four at a time
-// as running sums, each thread sums 5 rows of those for its 4 x 2 outputs,
-// and a running sum over the last five planes (a register ring indexed at
-// compile time: the plane loop is unrolled by five) gives the sum along z.
+// One block of 288 threads produces a 64 x 32 column of outputs and walks it
+// along z with one barrier per input plane.  Per input plane: eight threads
+// per row of the 68 x 36 neighbourhood each form nine consecutive hashes
+// (five finalisers, halves picked by the run's parity; the per-row keys
+// m(m(a ^ z) ^ y) are formed one plane ahead by 36 threads), take the next
+// thread's first four hashes by a warp shuffle (a row's eight threads are
+// consecutive lanes of one warp) and write their nine 5-wide sums along x
+// into one of two x-sum buffers; after the barrier each of the first 256
+// threads sums 5 rows of those for its 4 x 2 outputs, and a running sum
+// over the last five planes (a register ring indexed at compile time: the
+// plane loop is unrolled by five) gives the sum along z.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,8 +30,10 @@
 
 namespace {
 
-constexpr int GX = 64, GY = 32, HX = GX + 4, HY = GY + 4;
-constexpr int SEG = 10, NSEG = 7, HXP = 72;   // hash row segments per thread; padded hash row (>= SEG * NSEG)
+constexpr int GX = 64, GY = 32, HY = GY + 4;
+constexpr int SEG = 9, NSEG = 8;          // hashes per thread, threads per row (columns 0..71 of the 68 needed)
+constexpr int kGenThreads = HY * NSEG;    // 288 = 9 warps, four rows per warp
+static_assert(32 % NSEG == 0, "a row's threads share one warp");
 
 __host__ __device__ __forceinline__ uint32_t fmix32(uint32_t u)
 {
@@ -44,8 +49,7 @@ struct GenCtx {
     uint32_t a;
     int64_t ox, oy, oz, nx, ny, nz, bx0, by0;
     int tx, ty;
-    int hrow, hseg;          // this thread's hash row and 10-wide segment (hrow >= HY: none)
-    bool odd;                // the tile's first hashed x (ox + bx0 - 2) is odd (the same for every segment)
+    int hrow, hseg;          // this thread's hash row and 9-wide run
     uint16_t *out[2];        // output rows 2ty, 2ty+1 of plane 0 at x = bx0 + 4tx (nullptr: past the box)
     int64_t plane;           // elements per output plane
     bool vec;                // four outputs as one 8-byte store
@@ -60,54 +64,51 @@ __device__ __forceinline__ void row_keys(const GenCtx &g, int64_t k, uint32_t *r
     }
 }
 
-// One input plane k: hashes, sums along x and y, the running sum along z
-// (ring slot J holds this plane's sums until five planes later), and the
-// output plane k - 2 once its five-plane window is complete.
+// One input plane k: hashes and sums along x (all threads), then, after the
+// block's barrier, sums along y, the running sum along z (ring slot J holds
+// this plane's sums until five planes later), and the output plane k - 2 once
+// its five-plane window is complete (the first 256 threads).
 template <int J>
-__device__ __forceinline__ void gen_plane(const GenCtx &g, int64_t k, uint32_t (*hs)[HXP], uint32_t (*xs)[GX],
-                                          uint32_t (*rk)[HY], uint32_t (&ring)[5][8], uint32_t (&zs)[8])
+__device__ __forceinline__ void gen_plane(const GenCtx &g, int64_t k, uint32_t (*xs)[HY][GX], uint32_t (*rk)[HY],
+                                          uint32_t (&ring)[5][8], uint32_t (&zs)[8])
 {
-    if (g.hrow < HY) {
-        // ten consecutive hashes of one row (the padding columns 68..71 are never read):
-        // halves of the finalisers of pairs floor(x/2) .. floor(x/2) + 4 (+ 5 when x starts odd)
+    {
+        row_keys(g, k + 1, rk[(k + 1) & 1]);   // read after this plane's barrier
         const uint32_t key = rk[k & 1][g.hrow];
-        const int64_t xs = g.ox + g.bx0 - 2 + SEG * g.hseg;
-        const uint32_t p0 = (uint32_t)((xs - (xs & 1)) / 2);
-        uint32_t *row = &hs[g.hrow][SEG * g.hseg];
-        if (!g.odd) {
+        const int64_t x0 = g.ox + g.bx0 - 2 + SEG * g.hseg;
+        const int64_t pe = (x0 - (x0 & 1)) / 2;   // floor(x0 / 2)
+        const bool odd = (x0 & 1) != 0;
+        uint32_t u[5];
 #pragma unroll
-            for (int j = 0; j < SEG / 2; j++) {
-                const uint32_t u = fmix32(key ^ (p0 + (uint32_t)j));
-                row[2 * j] = u & 0xFFFFu;
-                row[2 * j + 1] = u >> 16;
-            }
-        } else {
-            row[0] = fmix32(key ^ p0) >> 16;
+        for (int i = 0; i < 5; i++) u[i] = fmix32(key ^ (uint32_t)(pe + i));
+        // hash of x0 + j: half ((j + odd) & 1) of u[(j + odd) >> 1]
+        uint32_t h[SEG + 4];
 #pragma unroll
-            for (int j = 1; j < SEG / 2; j++) {
-                const uint32_t u = fmix32(key ^ (p0 + (uint32_t)j));
-                row[2 * j - 1] = u & 0xFFFFu;
-                row[2 * j] = u >> 16;
+        for (int j = 0; j < SEG; j++) {
+            const uint32_t ev = (j & 1) ? (u[j >> 1] >> 16) : (u[j >> 1] & 0xFFFFu);
+            const uint32_t od = ((j + 1) & 1) ? (u[(j + 1) >> 1] >> 16) : (u[(j + 1) >> 1] & 0xFFFFu);
+            h[j] = odd ? od : ev;
+        }
+        // the next run's first four hashes (the row's last thread needs none)
+#pragma unroll
+        for (int j = 0; j < 4; j++) h[SEG + j] = __shfl_down_sync(0xffffffffu, h[j], 1);
+        uint32_t *xr = xs[k & 1][g.hrow];
+        const int c0 = SEG * g.hseg;
+        uint32_t sum = h[0] + h[1] + h[2] + h[3] + h[4];
+        xr[c0] = sum;   // c0 <= 63
+        if (g.hseg < NSEG - 1) {
+#pragma unroll
+            for (int i = 1; i < SEG; i++) {
+                sum += h[i + 4] - h[i - 1];
+                xr[c0 + i] = sum;
             }
-            row[SEG - 1] = fmix32(key ^ (p0 + (uint32_t)(SEG / 2))) & 0xFFFFu;
         }
     }
     __syncthreads();
-    row_keys(g, k + 1, rk[(k + 1) & 1]);   // next plane's keys (read after the next barrier)
-    for (int i = threadIdx.x; i < HY * (GX / 4); i += blockDim.x) {
-        const int ly = i >> 4, q = i & 15;
-        const uint4 a = *(const uint4 *)&hs[ly][4 * q], b = *(const uint4 *)&hs[ly][4 * q + 4];
-        uint4 o;
-        o.x = a.x + a.y + a.z + a.w + b.x;
-        o.y = o.x - a.x + b.y;
-        o.z = o.y - a.y + b.z;
-        o.w = o.z - a.z + b.w;
-        *(uint4 *)&xs[ly][4 * q] = o;
-    }
-    __syncthreads();
+    if (threadIdx.x >= 256) return;   // no outputs of its own
     uint4 r[6];
 #pragma unroll
-    for (int j = 0; j < 6; j++) r[j] = *(const uint4 *)&xs[2 * g.ty + j][4 * g.tx];
+    for (int j = 0; j < 6; j++) r[j] = *(const uint4 *)&xs[k & 1][2 * g.ty + j][4 * g.tx];
     uint32_t s[8];
     s[0] = r[0].x + r[1].x + r[2].x + r[3].x + r[4].x;
     s[1] = r[0].y + r[1].y + r[2].y + r[3].y + r[4].y;
@@ -142,12 +143,12 @@ __device__ __forceinline__ void gen_plane(const GenCtx &g, int64_t k, uint32_t (
     }
 }
 
-__global__ void __launch_bounds__(256, 3) k_hashbox(uint64_t seed, int64_t ox, int64_t oy, int64_t oz, int64_t nx,
-                                                 int64_t ny, int64_t nz, uint16_t *__restrict__ dst)
+__global__ void __launch_bounds__(kGenThreads, 2) k_hashbox(uint64_t seed, int64_t ox, int64_t oy, int64_t oz,
+                                                         int64_t nx, int64_t ny, int64_t nz,
+                                                         uint16_t *__restrict__ dst)
 {
-    __shared__ __align__(16) uint32_t hs[HY][HXP];  // hashes of the plane's neighbourhood
-    __shared__ __align__(16) uint32_t xs[HY][GX];   // 5-wide sums along x
-    __shared__ uint32_t rk[2][HY];                  // row keys of this plane and the next
+    __shared__ __align__(16) uint32_t xs[2][HY][GX];   // 5-wide sums along x, this plane and the next
+    __shared__ uint32_t rk[2][HY];                     // row keys of this plane and the next
     GenCtx g;
     g.a = fmix32((uint32_t)seed ^ fmix32((uint32_t)(seed >> 32)));
     g.ox = ox; g.oy = oy; g.oz = oz; g.nx = nx; g.ny = ny; g.nz = nz;
@@ -157,7 +158,6 @@ __global__ void __launch_bounds__(256, 3) k_hashbox(uint64_t seed, int64_t ox, i
     g.ty = threadIdx.x >> 4;   // outputs y 2ty, 2ty+1
     g.hrow = threadIdx.x / NSEG;
     g.hseg = threadIdx.x - g.hrow * NSEG;
-    g.odd = ((ox + g.bx0 - 2) & 1) != 0;
     g.plane = ny * nx;
     const int64_t x = g.bx0 + 4 * g.tx;
     for (int yy = 0; yy < 2; yy++) {
@@ -174,15 +174,15 @@ __global__ void __launch_bounds__(256, 3) k_hashbox(uint64_t seed, int64_t ox, i
         for (int a = 0; a < 5; a++) ring[a][b] = 0;
     }
     row_keys(g, -2, rk[(-2) & 1]);
-    __syncthreads();
+    __syncthreads();   // the first plane's keys
     // input planes -2 .. nz+1; ring slot = (k + 2) mod 5
     const int64_t kend = nz + 2;
     for (int64_t k = -2; k < kend; k += 5) {
-        gen_plane<0>(g, k, hs, xs, rk, ring, zs);
-        if (k + 1 < kend) gen_plane<1>(g, k + 1, hs, xs, rk, ring, zs);
-        if (k + 2 < kend) gen_plane<2>(g, k + 2, hs, xs, rk, ring, zs);
-        if (k + 3 < kend) gen_plane<3>(g, k + 3, hs, xs, rk, ring, zs);
-        if (k + 4 < kend) gen_plane<4>(g, k + 4, hs, xs, rk, ring, zs);
+        gen_plane<0>(g, k, xs, rk, ring, zs);
+        if (k + 1 < kend) gen_plane<1>(g, k + 1, xs, rk, ring, zs);
+        if (k + 2 < kend) gen_plane<2>(g, k + 2, xs, rk, ring, zs);
+        if (k + 3 < kend) gen_plane<3>(g, k + 3, xs, rk, ring, zs);
+        if (k + 4 < kend) gen_plane<4>(g, k + 4, xs, rk, ring, zs);
     }
 }
 
@@ -197,7 +197,7 @@ extern "C" int ec_gen_hashbox_u16(uint64_t seed, int64_t x0, int64_t y0, int64_t
     if (nx < 1 || ny < 1 || nz < 1 || !dst_dev) { set_error("bad hash-box request"); return EC_ERR_ARG; }
     if ((nx + GX - 1) / GX > INT32_MAX || (ny + GY - 1) / GY > 65535) { set_error("hash box too wide"); return EC_ERR_ARG; }
     dim3 grid((unsigned)((nx + GX - 1) / GX), (unsigned)((ny + GY - 1) / GY));
-    k_hashbox<<<grid, 256, 0, (cudaStream_t)stream>>>(seed, x0, y0, z0, nx, ny, nz, (uint16_t *)dst_dev);
+    k_hashbox<<<grid, kGenThreads, 0, (cudaStream_t)stream>>>(seed, x0, y0, z0, nx, ny, nz, (uint16_t *)dst_dev);
     EC_CUDA(cudaGetLastError());
     return EC_OK;
 }
