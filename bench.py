@@ -279,10 +279,10 @@ def config5_section(ec, ctx, n_requests, seed=5, loads=(0.5, 0.9, 1.2), with_ora
               "fields": "device-resident (read in place); thresholds and outputs through host memory",
               "loads": []}
     rng = np.random.default_rng(seed)
-    for rho in loads:
+
+    def poisson_pass(rho):
         rate = rho * len(reqs_sv) / cap_s
         gaps = rng.exponential(1.0 / rate, size=len(reqs_sv))
-        sv.reset_stats()
         t0 = time.perf_counter()
         due = t0
         tickets = []
@@ -291,8 +291,17 @@ def config5_section(ec, ctx, n_requests, seed=5, loads=(0.5, 0.9, 1.2), with_ora
             while time.perf_counter() < due:
                 pass
             tickets.append(sv.submit(**r))
-        served_ok &= all(np.array_equal(sv.wait(t, 600000), w) for t, w in zip(tickets, want))
-        span = time.perf_counter() - t0
+        ok = all(np.array_equal(sv.wait(t, 600000), w) for t, w in zip(tickets, want))
+        return rate, time.perf_counter() - t0, ok
+
+    # untimed pass at the lowest load: the groups that arrivals form (smaller
+    # than the closed loop's) meet their mix classes, so tuning stays out of
+    # the timed passes
+    served_ok &= poisson_pass(loads[0])[2]
+    for rho in loads:
+        sv.reset_stats()
+        rate, span, ok = poisson_pass(rho)
+        served_ok &= ok
         st = sv.stats()
         served["loads"].append({"offered_load": rho, "offered_rate_req_s": rate, "gcells_s": cells / span / 1e9,
                                 "p50_us": st["p50_us"], "p99_us": st["p99_us"], "mean_us": st["mean_us"]})
