@@ -39,6 +39,83 @@ namespace {
 
 int dtype_size(int dtype) { return dtype == EC_F32 ? 4 : (dtype == EC_U16 ? 2 : 1); }
 
+// Reader threads kept in the context for raw-file streaming: each slab's
+// byte range is split into nthr contiguous parts read in parallel
+// (page-cache copies are bound by per-core memory bandwidth, so more readers
+// read faster).
+struct ReaderPool {
+    std::vector<std::thread> th;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::function<void(int)> job;
+    uint64_t gen = 0;
+    int pending = 0;
+    bool stop = false;
+    explicit ReaderPool(int n)
+    {
+        for (int t = 1; t < n; t++)
+            th.emplace_back([this, t]() {
+                uint64_t seen = 0;
+                for (;;) {
+                    std::function<void(int)> fn;
+                    {
+                        std::unique_lock<std::mutex> lk(mu);
+                        cv.wait(lk, [&] { return stop || gen != seen; });
+                        if (stop) return;
+                        seen = gen;
+                        fn = job;
+                    }
+                    fn(t);
+                    std::lock_guard<std::mutex> lk(mu);
+                    if (--pending == 0) done_cv.notify_one();
+                }
+            });
+    }
+    int size() const { return (int)th.size() + 1; }
+    // run fn(0 .. size()-1), part 0 on the calling thread
+    void run(const std::function<void(int)> &fn)
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            job = fn;
+            pending = (int)th.size();
+            gen++;
+        }
+        cv.notify_all();
+        fn(0);
+        std::unique_lock<std::mutex> lk(mu);
+        done_cv.wait(lk, [&] { return pending == 0; });
+    }
+    ~ReaderPool()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stop = true;
+        }
+        cv.notify_all();
+        for (auto &x : th) x.join();
+    }
+};
+
+// Page-locked staging of raw-file streaming, kept in the context between
+// calls (grown when a call needs more; used only inside the streaming call,
+// which holds the context's lock): two buffers, an event per buffer marking
+// the copy that last read it, and the reader pool.
+struct FileStaging {
+    void *pinned[2] = {nullptr, nullptr};
+    size_t cap = 0;
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    ReaderPool *pool = nullptr;
+    ~FileStaging()
+    {
+        delete pool;
+        for (int i = 0; i < 2; i++) {
+            if (copied[i]) { cudaEventSynchronize(copied[i]); cudaEventDestroy(copied[i]); }
+            if (pinned[i]) cudaFreeHost(pinned[i]);
+        }
+    }
+};
+
 // Streams, events and device memory of the streaming path, kept in the
 // context between calls (the memory is reallocated when a call needs more, or
 // when it would not fit the call's cap).
@@ -47,8 +124,10 @@ struct StreamRes {
     size_t bytes = 0;
     cudaStream_t comp = nullptr, side = nullptr;
     cudaEvent_t filled[3] = {nullptr, nullptr, nullptr}, freed[3] = {nullptr, nullptr, nullptr};
+    FileStaging *file = nullptr;
     ~StreamRes()
     {
+        delete file;
         if (comp) cudaStreamSynchronize(comp);
         if (side) cudaStreamSynchronize(side);
         for (int i = 0; i < 3; i++) {
@@ -220,83 +299,50 @@ extern "C" int ec_curve_3d_stream(ec_ctx *ctx, const void *host_field, ec_slab_f
 
 namespace {
 
-// Reader threads that live for one call: each slab's byte range is split
-// into nthr contiguous parts read in parallel (page-cache copies are bound
-// by per-core memory bandwidth, so more readers read faster).
-struct ReaderPool {
-    std::vector<std::thread> th;
-    std::mutex mu;
-    std::condition_variable cv, done_cv;
-    std::function<void(int)> job;
-    uint64_t gen = 0;
-    int pending = 0;
-    bool stop = false;
-    explicit ReaderPool(int n)
-    {
-        for (int t = 1; t < n; t++)
-            th.emplace_back([this, t]() {
-                uint64_t seen = 0;
-                for (;;) {
-                    std::function<void(int)> fn;
-                    {
-                        std::unique_lock<std::mutex> lk(mu);
-                        cv.wait(lk, [&] { return stop || gen != seen; });
-                        if (stop) return;
-                        seen = gen;
-                        fn = job;
-                    }
-                    fn(t);
-                    std::lock_guard<std::mutex> lk(mu);
-                    if (--pending == 0) done_cv.notify_one();
-                }
-            });
-    }
-    int size() const { return (int)th.size() + 1; }
-    // run fn(0 .. size()-1), part 0 on the calling thread
-    void run(const std::function<void(int)> &fn)
-    {
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            job = fn;
-            pending = (int)th.size();
-            gen++;
-        }
-        cv.notify_all();
-        fn(0);
-        std::unique_lock<std::mutex> lk(mu);
-        done_cv.wait(lk, [&] { return pending == 0; });
-    }
-    ~ReaderPool()
-    {
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            stop = true;
-        }
-        cv.notify_all();
-        for (auto &x : th) x.join();
-    }
-};
-
 struct FileSlabs {
     int fd = -1;
     int64_t offset = 0, d = 0;
-    size_t plane = 0, cap = 0;          // bytes per plane, bytes per staging buffer
-    void *pinned[2] = {nullptr, nullptr};
-    cudaEvent_t copied[2] = {nullptr, nullptr};
+    size_t plane = 0, cap = 0;          // bytes per plane, bytes a staging buffer needs
+    FileStaging *st = nullptr;          // the context's staging
     int next = 0;
     int64_t bad_plane = -1;             // first plane whose read failed
     int bad_errno = 0;
-    ReaderPool *pool = nullptr;
+    bool staging_failed = false;
     ~FileSlabs()
     {
-        delete pool;
-        for (int i = 0; i < 2; i++) {
-            if (copied[i]) { cudaEventSynchronize(copied[i]); cudaEventDestroy(copied[i]); }
-            if (pinned[i]) cudaFreeHost(pinned[i]);
-        }
         if (fd >= 0) close(fd);
     }
 };
+
+// Staging of at least f.cap bytes per buffer, events and readers (inside the
+// streaming call, under the context's lock).
+int file_staging_ready(FileSlabs &f)
+{
+    FileStaging &st = *f.st;
+    for (int i = 0; i < 2; i++)
+        if (!st.copied[i] && cudaEventCreateWithFlags(&st.copied[i], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            st.copied[i] = nullptr;
+            return 1;
+        }
+    if (st.cap < f.cap) {
+        for (int i = 0; i < 2; i++) {
+            if (cudaEventSynchronize(st.copied[i]) != cudaSuccess) return 1;
+            if (st.pinned[i]) cudaFreeHost(st.pinned[i]);
+            st.pinned[i] = nullptr;
+        }
+        st.cap = 0;
+        for (int i = 0; i < 2; i++)
+            if (cudaMallocHost(&st.pinned[i], f.cap) != cudaSuccess) {
+                cudaGetLastError();
+                st.pinned[i] = nullptr;
+                return 1;
+            }
+        st.cap = f.cap;
+    }
+    if (!st.pool) st.pool = new ReaderPool((int)std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
+    return 0;
+}
 
 int file_producer(void *user, int64_t z0, int64_t z1, void *dst_dev, void *stream)
 {
@@ -305,19 +351,21 @@ int file_producer(void *user, int64_t z0, int64_t z1, void *dst_dev, void *strea
     if (b <= a) return 0;
     const size_t bytes = (size_t)(b - a) * f.plane;
     if (bytes > f.cap) return 1;
+    if (file_staging_ready(f)) { f.staging_failed = true; return 6; }
+    FileStaging &st = *f.st;
     const int i = f.next;
     f.next ^= 1;
-    if (cudaEventSynchronize(f.copied[i]) != cudaSuccess) return 2;
+    if (cudaEventSynchronize(st.copied[i]) != cudaSuccess) return 2;
     // the slab's bytes in equal contiguous parts, one per reader (parts of at
     // least 1 MiB)
-    const int nthr = (int)std::max<size_t>(1, std::min<size_t>((size_t)f.pool->size(), bytes >> 20));
+    const int nthr = (int)std::max<size_t>(1, std::min<size_t>((size_t)st.pool->size(), bytes >> 20));
     const int64_t base_off = f.offset + a * (int64_t)f.plane;
     std::vector<int64_t> bad(nthr, -1);
     std::vector<int> bad_err(nthr, 0);
     auto read_part = [&](int t) {
         if (t >= nthr) return;
         const size_t b0 = bytes * (size_t)t / (size_t)nthr, b1 = bytes * (size_t)(t + 1) / (size_t)nthr;
-        char *p = (char *)f.pinned[i] + b0;
+        char *p = (char *)st.pinned[i] + b0;
         off_t off = (off_t)(base_off + (int64_t)b0);
         size_t left = b1 - b0;
         while (left > 0) {
@@ -334,7 +382,7 @@ int file_producer(void *user, int64_t z0, int64_t z1, void *dst_dev, void *strea
         }
     };
     if (nthr == 1) read_part(0);
-    else f.pool->run(read_part);
+    else st.pool->run(read_part);
     for (int t = 0; t < nthr; t++)
         if (bad[t] >= 0) {
             f.bad_plane = bad[t];
@@ -342,10 +390,10 @@ int file_producer(void *user, int64_t z0, int64_t z1, void *dst_dev, void *strea
             return 3;
         }
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemcpyAsync((char *)dst_dev + (size_t)(a - z0) * f.plane, f.pinned[i], bytes, cudaMemcpyHostToDevice,
+    if (cudaMemcpyAsync((char *)dst_dev + (size_t)(a - z0) * f.plane, st.pinned[i], bytes, cudaMemcpyHostToDevice,
                         s) != cudaSuccess)
         return 4;
-    if (cudaEventRecord(f.copied[i], s) != cudaSuccess) return 5;
+    if (cudaEventRecord(st.copied[i], s) != cudaSuccess) return 5;
     return 0;
 }
 
@@ -380,20 +428,19 @@ extern "C" int ec_curve_3d_file(ec_ctx *ctx, const char *path, int64_t offset, c
     // a slab asks for at most min(slab_planes, d) + 2 planes (halo planes outside the file are not read)
     f.cap = (size_t)(std::min<int64_t>(slab_planes, dims[0]) + 2) * f.plane;
     {
-        DeviceGuard dg(ctx->device);
-        for (int i = 0; i < 2; i++) {
-            if (cudaMallocHost(&f.pinned[i], f.cap) != cudaSuccess) {
-                cudaGetLastError();
-                f.pinned[i] = nullptr;
-                set_error("cannot allocate %zu bytes of page-locked staging", f.cap);
-                return EC_ERR_OOM;
-            }
-            EC_CUDA(cudaEventCreateWithFlags(&f.copied[i], cudaEventDisableTiming));
-        }
+        // the context's staging holder (its buffers are sized inside the call)
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        if (!ctx->stream_state) ctx->stream_state = new StreamRes();
+        StreamRes &res = *(StreamRes *)ctx->stream_state;
+        if (!res.file) res.file = new FileStaging();
+        f.st = res.file;
     }
-    f.pool = new ReaderPool((int)std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
     rc = ec_curve_3d_stream(ctx, nullptr, file_producer, &f, dims, dtype, thresholds_host, L, connectivity,
                             descriptors, slab_planes, device_mem_cap, out_host);
+    if (rc && f.staging_failed) {
+        set_error("cannot allocate %zu bytes of page-locked staging", f.cap);
+        return EC_ERR_OOM;
+    }
     if (rc && f.bad_plane >= 0) {
         set_error("reading plane %lld of %s failed: %s", (long long)f.bad_plane, path,
                   f.bad_errno ? strerror(f.bad_errno) : "end of file");
