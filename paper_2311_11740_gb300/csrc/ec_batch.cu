@@ -402,6 +402,8 @@ using namespace ec::batch;
 
 namespace {
 
+constexpr int kPlanarBranches = 4;
+
 struct BatchState {
     void *dev = nullptr;
     size_t dev_bytes = 0;
@@ -409,7 +411,8 @@ struct BatchState {
     size_t staging_bytes = 0;
     cudaEvent_t staged_free = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;   // capture-time branch of the planar launches
+    cudaEvent_t fork = nullptr;                   // capture-time branches of the planar launches (kPlanarBranches)
+    cudaEvent_t join[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 }  // namespace
@@ -657,28 +660,43 @@ static int batch_run(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, cudaSt
                            ctx->ws, s);
         if (rc) return rc;
     }
-    // the planar fields' launch sequences (scratch sized first: none is
-    // allocated while a graph is captured)
+    // the planar fields' launch sequences on up to kPlanarBranches parallel
+    // branches (fields, largest first, to the branch with the fewest voxels
+    // so far), each with its own part of the context's scratch (sized first:
+    // none is allocated while a graph is captured) and half the GPU's blocks
+    // per launch, so that two fields share the GPU with deeper work items
+    const int nbr = (int)std::min<size_t>(kPlanarBranches, planar.size());
+    std::vector<std::vector<int>> branch(nbr);
+    {
+        std::vector<int64_t> load(nbr, 0);
+        for (int i : planar) {
+            const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            branch[k].push_back(i);
+            load[k] += vox(i);
+        }
+    }
     size_t planar_scratch = 0;
     for (int i : planar)
         planar_scratch = std::max(planar_scratch, curve_scratch_bytes(fields[i].descriptors, fields[i].L));
+    planar_scratch = (planar_scratch + 255) & ~(size_t)255;
     if (!planar.empty()) {
-        const int rc = ensure_scratch(ctx, planar_scratch);
+        const int rc = ensure_scratch(ctx, (size_t)nbr * planar_scratch);
         if (rc) return rc;
     }
-    auto enqueue_planar = [&](cudaStream_t st) -> int {
-        for (int i : planar) {
+    auto enqueue_branch = [&](int k, cudaStream_t st) -> int {
+        for (int i : branch[k]) {
             const ec_field_desc &d = fields[i];
             CurvePlan cp;
             cp.algo = ALGO_PLANAR;
             cp.num_sms = ctx->num_sms;
+            cp.grid = nbr > 1 ? ctx->num_sms : 0;
             const int rc = enqueue_curve(cp, 3, d.field, d.dims, d.dtype, d.thresholds, d.L, d.connectivity,
-                                         d.descriptors, d.out, ctx->ws, st);
+                                         d.descriptors, d.out, (char *)ctx->ws + (size_t)k * planar_scratch, st);
             if (rc) return rc;
         }
         return EC_OK;
     };
-    if (bf.empty()) return enqueue_planar(s);
+    if (bf.empty() && planar.empty()) return EC_OK;
     if (items.size() > (size_t)INT32_MAX) { set_error("batch too large"); return EC_ERR_UNSUPPORTED; }
 
     // ---- device layout: [flags 256][fields][items][counters][hist]
@@ -706,7 +724,8 @@ static int batch_run(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, cudaSt
     }
     if (!st.staged_free) EC_CUDA(cudaEventCreateWithFlags(&st.staged_free, cudaEventDisableTiming));
     if (!st.fork) EC_CUDA(cudaEventCreateWithFlags(&st.fork, cudaEventDisableTiming));
-    if (!st.join) EC_CUDA(cudaEventCreateWithFlags(&st.join, cudaEventDisableTiming));
+    for (int k = 0; k < kPlanarBranches; k++)
+        if (!st.join[k]) EC_CUDA(cudaEventCreateWithFlags(&st.join[k], cudaEventDisableTiming));
     char *base = (char *)st.dev;
     int *flags = (int *)base;
     BField *d_fields = (BField *)(base + 256);
@@ -714,8 +733,8 @@ static int batch_run(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, cudaSt
     int *d_counters = (int *)(base + 256 + fb_bytes + it_bytes);
     long long *d_hist = (long long *)(base + 256 + fb_bytes + it_bytes + ct_bytes);
     for (auto &F : bf) F.hist = d_hist + (size_t)(uintptr_t)F.hist;
-    memcpy(st.staging, bf.data(), bf.size() * sizeof(BField));
-    memcpy((char *)st.staging + fb_bytes, items.data(), items.size() * sizeof(BItem));
+    if (!bf.empty()) memcpy(st.staging, bf.data(), bf.size() * sizeof(BField));
+    if (!items.empty()) memcpy((char *)st.staging + fb_bytes, items.data(), items.size() * sizeof(BItem));
 
     // ---- launch configuration
     const size_t hist_cap = std::max<size_t>(max_smem_entries, 1);
@@ -727,33 +746,38 @@ static int batch_run(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, cudaSt
     grid = std::min<int>(grid, (int)items.size());
 
     // ---- capture the sequence into a graph; update the cached executable if possible
-    // the planar fields run on a second branch of the same graph, beside
+    // the planar fields run on further branches of the same graph, beside
     // the persistent kernel
-    cudaStream_t cap = nullptr, cap2 = nullptr;
+    cudaStream_t cap = nullptr, capb[kPlanarBranches] = {};
     EC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    if (!planar.empty() && cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaStreamDestroy(cap);
-        return cuda_fail(cudaGetLastError(), "batch stream creation");
-    }
+    for (int k = 0; k < nbr; k++)
+        if (cudaStreamCreateWithFlags(&capb[k], cudaStreamNonBlocking) != cudaSuccess) {
+            for (int j = 0; j < k; j++) cudaStreamDestroy(capb[j]);
+            cudaStreamDestroy(cap);
+            return cuda_fail(cudaGetLastError(), "batch stream creation");
+        }
     cudaGraph_t graph = nullptr;
     int prc = EC_OK;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        if (cap2) {
-            cudaEventRecord(st.fork, cap);
-            cudaStreamWaitEvent(cap2, st.fork, 0);
-            prc = enqueue_planar(cap2);
-            cudaEventRecord(st.join, cap2);
+        if (nbr > 0) cudaEventRecord(st.fork, cap);
+        for (int k = 0; k < nbr; k++) {
+            cudaStreamWaitEvent(capb[k], st.fork, 0);
+            if (!prc) prc = enqueue_branch(k, capb[k]);
+            cudaEventRecord(st.join[k], capb[k]);
         }
-        cudaMemcpyAsync(d_fields, st.staging, table_bytes, cudaMemcpyHostToDevice, cap);
-        cudaMemsetAsync(flags, 0, 256, cap);
-        cudaMemsetAsync(d_counters, 0, ct_bytes + hs_bytes, cap);
-        k_batch<<<grid, kThreads, smem, cap>>>(d_fields, d_items, (int)items.size(), d_counters, flags, hist_cap);
-        if (cap2) cudaStreamWaitEvent(cap, st.join, 0);
+        if (!items.empty()) {
+            cudaMemcpyAsync(d_fields, st.staging, table_bytes, cudaMemcpyHostToDevice, cap);
+            cudaMemsetAsync(flags, 0, 256, cap);
+            cudaMemsetAsync(d_counters, 0, ct_bytes + hs_bytes, cap);
+            k_batch<<<grid, kThreads, smem, cap>>>(d_fields, d_items, (int)items.size(), d_counters, flags,
+                                                   hist_cap);
+        }
+        for (int k = 0; k < nbr; k++) cudaStreamWaitEvent(cap, st.join[k], 0);
         e = cudaStreamEndCapture(cap, &graph);
     }
     cudaStreamDestroy(cap);
-    if (cap2) cudaStreamDestroy(cap2);
+    for (int k = 0; k < nbr; k++) cudaStreamDestroy(capb[k]);
     if (prc) { if (graph) cudaGraphDestroy(graph); return prc; }
     if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(e, "batch graph capture"); }
     bool updated = false;
@@ -786,7 +810,8 @@ void ec::batch_release(ec_ctx *ctx)
     if (st->exec) cudaGraphExecDestroy(st->exec);
     if (st->staged_free) cudaEventDestroy(st->staged_free);
     if (st->fork) cudaEventDestroy(st->fork);
-    if (st->join) cudaEventDestroy(st->join);
+    for (int k = 0; k < 4; k++)
+        if (st->join[k]) cudaEventDestroy(st->join[k]);
     if (st->dev) cudaFree(st->dev);
     if (st->staging) cudaFreeHost(st->staging);
     delete st;
