@@ -13,10 +13,14 @@ sensor frames of 36 small tiles served one frame at a time, and the 2048^3
 low-memory workload streamed from its on-device generator under a 4 GB cap.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-  python bench.py --profile-case [typemap|2d]   (the curve kernel, or the
-                                      type map, alone on a 256 x 512 x 512 slab
-                                      of the field; or the 2D kernel on the
-                                      16384^2 uint8 field; for ncu captures)
+  python bench.py --profile-case [typemap|2d|rows|hashbox]
+                                     (the curve kernel, or the type map, alone
+                                      on a 256 x 512 x 512 slab of the field;
+                                      the 2D kernel on the 16384^2 uint8 field;
+                                      the curve kernel on a 256 x 511 x 511
+                                      slab (rows not a multiple of 16 bytes);
+                                      or one 66-plane slab of the 2048^2
+                                      hash-box generator; for ncu captures)
 
 --impl reference times the CPU oracle (the plain cell-counting reference) on
 this machine's host cores, on a bounded sample of the same workload.
@@ -646,7 +650,7 @@ def main():
     ap.add_argument("--batch-requests", type=int, default=4096)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-type-map", action="store_true")
-    ap.add_argument("--profile-case", nargs="?", const="curve", choices=("curve", "typemap", "2d"),
+    ap.add_argument("--profile-case", nargs="?", const="curve", choices=("curve", "typemap", "2d", "rows", "hashbox"),
                     help="run two curve requests (or two type maps) on the first 256 planes of the field, or "
                          "two 2D requests on the 16384^2 uint8 field (2d), and exit")
     args = ap.parse_args()
@@ -666,6 +670,13 @@ def main():
         dist.init_process_group("nccl")
     from paper_2311_11740_gb300 import ec, workloads
 
+    if args.profile_case == "hashbox":
+        for _ in range(2):
+            slab = ec.gen_hashbox_u16(4, 0, 0, 0, 2048, 2048, 66, device=local)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "2048 x 2048 x 66 uint16 hash-box slab (seed 4)",
+                          "value_at_origin": int(slab[0, 0, 0])}))
+        return 0
     if args.profile_case == "2d":
         u8, _, _ = workloads.config2(device="cuda")
         ctx = ec.Context(local)
@@ -678,6 +689,15 @@ def main():
         return 0
     n = args.small or N
     field, thr = workloads.config3(device="cuda", n=n) if args.small else workloads.config3(device="cuda")
+    if args.profile_case == "rows":
+        slab = field[:256, :511, :511].contiguous()
+        ctx = ec.Context(local)
+        for _ in range(2):
+            res = ec.curve(slab, thr, descriptors=DESC, ctx=ctx)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "256x511x511 float32 slab of the benchmark field (rows of 2044 bytes), "
+                                          "EC+area+volume", "volume_at_top": int(res[2, -1])}))
+        return 0
     if args.profile_case:
         slab = field[:256].contiguous()
         ctx = ec.Context(local)

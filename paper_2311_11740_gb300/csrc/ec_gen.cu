@@ -33,6 +33,9 @@ namespace {
 constexpr int GX = 64, GY = 32, HY = GY + 4;
 constexpr int SEG = 9, NSEG = 8;          // hashes per thread, threads per row (columns 0..71 of the 68 needed)
 constexpr int kGenThreads = HY * NSEG;    // 288 = 9 warps, four rows per warp
+// x-sum row pitch: 72 words put the four rows of a warp's nine-wide stores on
+// distinct banks (rows 64 words apart would share 8 banks four times over)
+constexpr int XP = GX + 8;
 static_assert(32 % NSEG == 0, "a row's threads share one warp");
 
 __host__ __device__ __forceinline__ uint32_t fmix32(uint32_t u)
@@ -69,7 +72,7 @@ __device__ __forceinline__ void row_keys(const GenCtx &g, int64_t k, uint32_t *r
 // this plane's sums until five planes later), and the output plane k - 2 once
 // its five-plane window is complete (the first 256 threads).
 template <int J>
-__device__ __forceinline__ void gen_plane(const GenCtx &g, int64_t k, uint32_t (*xs)[HY][GX], uint32_t (*rk)[HY],
+__device__ __forceinline__ void gen_plane(const GenCtx &g, int64_t k, uint32_t (*xs)[HY][XP], uint32_t (*rk)[HY],
                                           uint32_t (&ring)[5][8], uint32_t (&zs)[8])
 {
     {
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(kGenThreads, 2) k_hashbox(uint64_t seed, int64
                                                          int64_t nx, int64_t ny, int64_t nz,
                                                          uint16_t *__restrict__ dst)
 {
-    __shared__ __align__(16) uint32_t xs[2][HY][GX];   // 5-wide sums along x, this plane and the next
+    __shared__ __align__(16) uint32_t xs[2][HY][XP];   // 5-wide sums along x, this plane and the next
     __shared__ uint32_t rk[2][HY];                     // row keys of this plane and the next
     GenCtx g;
     g.a = fmix32((uint32_t)seed ^ fmix32((uint32_t)(seed >> 32)));
