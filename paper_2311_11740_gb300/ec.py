@@ -48,6 +48,8 @@ _lock = threading.Lock()
 def lib():
     """The loaded libec.so; raises if it has not been built."""
     global _lib
+    if _lib is not None:
+        return _lib
     with _lock:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
@@ -171,10 +173,22 @@ def default_context(device: int = 0) -> Context:
     return _default_ctx[device]
 
 
+_RAW_STREAM = None
+
+
 def _stream_ptr(stream, device):
+    """The CUDA stream handle to launch on: `stream`'s, else the device's
+    current stream (read without building a Stream object when torch offers
+    that)."""
+    global _RAW_STREAM
     import torch
-    s = stream if stream is not None else torch.cuda.current_stream(device)
-    return ctypes.c_void_p(s.cuda_stream)
+    if stream is not None:
+        return ctypes.c_void_p(stream.cuda_stream)
+    if _RAW_STREAM is None:
+        _RAW_STREAM = getattr(torch._C, "_cuda_getCurrentRawStream", False)
+    if _RAW_STREAM:
+        return ctypes.c_void_p(_RAW_STREAM(device))
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
 def curve(field, thresholds=None, L=None, connectivity=None, descriptors=EC_DESC_EC, out=None,
