@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "ec_internal.h"
 #include "ec_rules.h"
 
@@ -623,7 +625,9 @@ int launch_scan(const long long *hist, int nd, int32_t L, const int32_t scale[kM
 {
     Scales sc;
     for (int i = 0; i < kMaxDesc; i++) sc.s[i] = scale[i] > 0 ? scale[i] : 1;
-    k_scan<<<nd, 1024, 0, s>>>(hist, L, sc, out, err_flag);
+    // one thread per level up to 1024 (short curves start fewer idle warps)
+    const int threads = (int)std::min<int64_t>(1024, std::max<int64_t>(32, ((int64_t)L + 31) / 32 * 32));
+    k_scan<<<nd, threads, 0, s>>>(hist, L, sc, out, err_flag);
     EC_CUDA(cudaGetLastError());
     return EC_OK;
 }
