@@ -117,7 +117,8 @@ int ec_ctx_destroy(ec_ctx *ctx);
  *    environment variable EC_AUTOTUNE_CACHE naming a file, tuned plans
  *    persist there as JSON.
  *  EC_OPT_TEST_GIVE_UP (testing the failure path only): 1 = in the next 3D
- *    curve requests on the float32 TMA path, every block gives up its first
+ *    curve requests on the float32 tensor-map path (the row-copy staging has
+ *    no bounded device wait), every block gives up its first
  *    bounded device wait at once, as if the staged plane had not arrived in
  *    time.  The copies already requested still land (the block waits for
  *    them, bounded) before it returns; the curves read INT64_MIN and, with
@@ -147,11 +148,13 @@ int ec_curve_2d(ec_ctx *ctx, const void *field_dev, const int64_t dims[2], int d
 /* EC / perimeter / area / volume curves of a 3D field resident on the device.
  * Same conventions; dims = {d, h, w}.  Algorithm 3 of the paper (Appendix),
  * Table 2 weights; 26-connectivity (or 6, see the conventions above).
- * Performance note (results do not depend on it): float32 fields whose start
- * is 16-byte aligned and whose row length is a multiple of 4 are staged by
- * the tensor memory accelerator; other fields that start 16-byte aligned by
- * asynchronous 16-byte copies; fields that start unaligned by plain loads
- * (slowest).  The same holds for ec_curve_2d's rows. */
+ * Performance note (results do not depend on it): float32 fields with at
+ * most 1024 levels whose start is 16-byte aligned run on the fastest kernel,
+ * their rows staged by the tensor memory accelerator when the row length is
+ * a multiple of 4 and by per-row asynchronous 16-byte copies otherwise
+ * (about 1.3x the time per voxel); other fields that start 16-byte aligned
+ * are staged by asynchronous 16-byte copies; fields that start unaligned by
+ * plain loads (slowest).  The same holds for ec_curve_2d's rows. */
 int ec_curve_3d(ec_ctx *ctx, const void *field_dev, const int64_t dims[3], int dtype,
                 const void *thresholds_dev, int32_t L, int connectivity,
                 uint32_t descriptors, int64_t *out_dev, void *stream);
@@ -220,8 +223,11 @@ typedef struct {
 
 /* Curves of n independent fields of uneven sizes, dtypes and level counts in
  * one persistent-kernel launch (Sec. 4 notes that small images parallelise
- * poorly one at a time).  All pointers in `fields` are device pointers.
- * Results are identical to n separate ec_curve_2d / ec_curve_3d calls.
+ * poorly one at a time), captured in a CUDA graph; 3D fields of at least
+ * 2^21 voxels that the fastest 3D kernel takes run as their own launches on
+ * parallel branches of the same graph.  All pointers in `fields` are device
+ * pointers.  Results are identical to n separate ec_curve_2d / ec_curve_3d
+ * calls.
  * With EC_OPT_AUTOTUNE the first batch of a mix class runs several times
  * (synchronously) while its plan is chosen. */
 int ec_batch(ec_ctx *ctx, const ec_field_desc *fields, int32_t n, void *stream);
